@@ -1,0 +1,135 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds no arithmetic of the sweeping method itself: only velocity
+fields c(x), right-hand sides f(x) and receiver/source placements, evaluated on
+the interior grid p_{i,j} = (i h, j h), 1 <= i, j <= n, h = 1/(n+1) (Section 2.1).
+
+Arrays are laid out row by row, x1 fastest: a field is an (n, n) array F with
+F[j-1, i-1] = F(i h, j h), matching the unknown ordering of Section 2.1.
+
+The paper's own velocity fields are only pictured (Section 3), so these are
+stand-ins with the same character: a converging Gaussian lens, a random smooth
+medium and point/Gaussian sources.
+"""
+import numpy as np
+
+__all__ = [
+    "grid", "velocity_constant", "velocity_lens", "smooth_noise", "velocity_random",
+    "source_gaussian", "source_delta", "source_positions", "workload",
+]
+
+
+def grid(n):
+    """Node coordinates x = (k+1) h, k = 0..n-1, and the spacing h = 1/(n+1)."""
+    h = 1.0 / (n + 1)
+    return (np.arange(n, dtype=np.float64) + 1.0) * h, h
+
+
+def velocity_constant(n, c0=1.0):
+    return np.full((n, n), float(c0))
+
+
+def velocity_lens(n):
+    """Converging Gaussian lens c = (4/3)(1 - 0.5 exp(-32 |x - (0.5, 0.5)|^2))."""
+    x, _ = grid(n)
+    X1, X2 = np.meshgrid(x, x, indexing="xy")
+    r2 = (X1 - 0.5) ** 2 + (X2 - 0.5) ** 2
+    return (4.0 / 3.0) * (1.0 - 0.5 * np.exp(-32.0 * r2))
+
+
+def _gauss_filter_1d(n, h, width):
+    """Truncated (4 width) Gaussian taps of standard deviation `width` (physical units)."""
+    rad = int(np.ceil(4.0 * width / h))
+    t = np.arange(-rad, rad + 1) * h
+    return np.exp(-0.5 * (t / width) ** 2)
+
+
+def smooth_noise(n, width, seed):
+    """Unit-std smooth field: i.i.d. N(0,1) on the nodes, separable Gaussian filter
+    with zero padding, divided by its population standard deviation."""
+    rng = np.random.default_rng(seed)
+    g0 = rng.standard_normal((n, n))
+    _, h = grid(n)
+    k = _gauss_filter_1d(n, h, width)
+    rad = (k.size - 1) // 2
+
+    def conv(v):  # zero-padded, centred, length n even when the taps outnumber v
+        return np.convolve(v, k, mode="full")[rad:rad + n]
+
+    g = np.apply_along_axis(conv, 1, g0)
+    g = np.apply_along_axis(conv, 0, g)
+    return g / g.std()
+
+
+def velocity_random(n, width, seed, amp=0.2):
+    """Random smooth medium c = 1 + amp * g."""
+    return 1.0 + amp * smooth_noise(n, width, seed)
+
+
+def source_gaussian(n, center=(0.5, 0.5), sigma=1.0 / 64.0):
+    """Unnormalised Gaussian f = exp(-|x - x0|^2 / (2 sigma^2)) (complex128)."""
+    x, _ = grid(n)
+    X1, X2 = np.meshgrid(x, x, indexing="xy")
+    r2 = (X1 - center[0]) ** 2 + (X2 - center[1]) ** 2
+    return np.exp(-r2 / (2.0 * sigma * sigma)).astype(np.complex128)
+
+
+def _nearest_node(n, t):
+    _, h = grid(n)
+    k = int(np.floor(t / h + 0.5)) - 1
+    return min(max(k, 0), n - 1)
+
+
+def source_delta(n, point):
+    """Discrete delta of mass one: 1/h^2 at the node nearest to `point`."""
+    _, h = grid(n)
+    f = np.zeros((n, n), dtype=np.complex128)
+    f[_nearest_node(n, point[1]), _nearest_node(n, point[0])] = 1.0 / (h * h)
+    return f
+
+
+def source_positions(n, count, pml_width, seed):
+    """`count` points uniform in [eta, 1 - eta]^2 with eta = pml_width * h."""
+    _, h = grid(n)
+    eta = pml_width * h
+    rng = np.random.default_rng(seed)
+    return rng.uniform(eta, 1.0 - eta, size=(count, 2))
+
+
+def workload(name):
+    """Named synthetic workloads (sizes, frequencies and inputs of the five
+    configurations the build is measured on).  Returns a dict with the
+    velocity field `c` (n, n), the right-hand sides `f` (nrhs, n, n) and the
+    solver settings.  `omega` is the angular frequency 2 pi (omega / 2 pi)."""
+    two_pi = 2.0 * np.pi
+    if name == "n64_const":
+        n = 64
+        return dict(name=name, n=n, omega=two_pi * 4, pml=8, eps_H=1e-9, tol=1e-8,
+                    c=velocity_constant(n), f=source_gaussian(n)[None])
+    if name == "n511_lens":
+        n = 511
+        return dict(name=name, n=n, omega=two_pi * 32, pml=12, eps_H=1e-6, tol=1e-6,
+                    c=velocity_lens(n), f=source_gaussian(n)[None])
+    if name in ("n1023_random", "n2047_random"):
+        big = name == "n2047_random"
+        n = 2047 if big else 1023
+        w, seed_c, seed_s, ns = (1 / 64, 5, 6, 16) if big else (1 / 32, 1, 2, 64)
+        pml = 16
+        pts = source_positions(n, ns, pml, seed_s)
+        f = np.stack([source_delta(n, p) for p in pts])
+        return dict(name=name, n=n, omega=two_pi * (128 if big else 64), pml=pml,
+                    eps_H=1e-6, tol=1e-7, c=velocity_random(n, w, seed_c), f=f)
+    if name == "n511_grad":
+        n = 511
+        _, h = grid(n)
+        pml = 12
+        eta = pml * h
+        xs = eta + (np.arange(32) + 0.5) * (1.0 - 2.0 * eta) / 32.0
+        f = np.stack([source_delta(n, (x, 0.9)) for x in xs])
+        rec_row = _nearest_node(n, 0.85)
+        rec_idx = rec_row * n + np.arange(n)
+        c_true = velocity_lens(n)
+        c = c_true + 0.05 * smooth_noise(n, 1 / 32, 3)
+        return dict(name=name, n=n, omega=two_pi * 32, pml=pml, eps_H=1e-6, tol=1e-8,
+                    c=c, c_true=c_true, f=f, rec_idx=rec_idx)
+    raise KeyError(name)
