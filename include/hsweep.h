@@ -1,0 +1,186 @@
+/*
+ * hsweep: sweeping preconditioner for the 2D Helmholtz equation with the
+ * Schur-complement inverses held as hierarchical (H-) matrices, on one GPU.
+ *
+ * Method: B. Engquist and L. Ying, "Sweeping preconditioner for the Helmholtz
+ * equation: hierarchical matrix representation" (2010).
+ *   - Section 2.1, Eq. sigma / Eq. helmd: PML stretching and the 5-point matrix A.
+ *   - Algorithm 2.5: setup sweep S~_m = A_mm - A_{m,m-1} T~_{m-1} A_{m-1,m},
+ *     T~_m = hinv(S~_m), every T~_m held as a weakly admissible H-matrix (Section 2.3).
+ *   - Algorithm 2.6: the apply u = M f (forward and backward sweeps of hmatvec).
+ *   - Section 2.4: GMRES on M A u = M f.
+ *
+ * Conventions used by every entry point below.
+ *   Grid:    n x n interior nodes p_{i,j} = (i h, j h), h = 1/(n+1), N = n*n.
+ *   Vectors: complex128 (hsw_c128), node (i, j) (1-based) at offset (j-1)*n + (i-1),
+ *            i.e. row by row with x1 fastest (Section 2.1 ordering).  A batch of
+ *            nrhs vectors is [nrhs][N], vector-major.
+ *   Memory:  unless stated otherwise, array arguments are DEVICE pointers; the caller
+ *            owns them.  The handle owns every internal buffer (factors, scratch).
+ *   Streams: all work is enqueued on the stream given to hsweep_setup.  Entry
+ *            points that report a result on the host (status codes from the device,
+ *            iteration counts, misfit) synchronise that stream before returning.
+ *   Errors:  every entry point returns an hsweep status code; on error no output
+ *            argument other than the status is guaranteed.  Nothing here calls
+ *            exit() or traps the GPU; device-side failures are recorded in a status
+ *            word read by hsweep_status.
+ *   Threads: a handle may be used by one host thread at a time.
+ */
+#ifndef HSWEEP_H
+#define HSWEEP_H
+
+#if defined(__GNUC__)
+#define HSWEEP_API __attribute__((visibility("default")))
+#else
+#define HSWEEP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsweep_s* hsweep_t;
+typedef struct { double re, im; } hsw_c128;
+
+/* Status codes. */
+enum {
+  HSWEEP_OK = 0,
+  HSWEEP_ERR_ARG = -1,           /* invalid argument (sizes, null pointers, NaN) */
+  HSWEEP_ERR_OOM = -2,           /* a device or host allocation failed; nothing leaked */
+  HSWEEP_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  HSWEEP_ERR_NUMERIC = -4,       /* zero pivot or non-finite value on the device */
+  HSWEEP_ERR_NOT_CONVERGED = -5, /* GMRES stopped at its iteration cap (best iterate kept) */
+  HSWEEP_ERR_TIMEOUT = -6        /* a bounded device-side wait ran out */
+};
+
+/* Arithmetic of the H-factors and of the sweeps. */
+enum {
+  HSWEEP_FP64 = 0,  /* complex128 everywhere */
+  HSWEEP_MIXED = 1  /* complex64 H-factors, setup products and sweeps; FP64 leaf
+                       inversions, GMRES (Arnoldi), residuals and iterative refinement */
+};
+
+typedef struct {
+  int leaf;          /* maximum leaf size of the cluster tree, 2..8 (default 8) */
+  int r_max;         /* rank cap of every factorised block, 1..64 (default 48) */
+  int precision;     /* HSWEEP_FP64 or HSWEEP_MIXED (default HSWEEP_MIXED) */
+  double pml_C;      /* PML constant C of Eq. sigma (default 2 pi) */
+  int pml_form;      /* 0: sigma = (C/eta)((t-eta)/eta)^2 as in Eq. sigma (default);
+                        1: sigma = C ((t-eta)/eta)^2 */
+  int gmres_max_it;  /* Arnoldi steps per GMRES solve (default 60) */
+  int refine_max;    /* outer FP64 refinement steps in HSWEEP_MIXED (default 8) */
+  int team;          /* CTAs per sweep team (power of two, 0 = automatic) */
+  int groups;        /* right-hand sides per sweep team (1, 2, 4 or 8; 0 = automatic) */
+} hsweep_opts;
+
+/* Fill *o with the defaults listed above. */
+HSWEEP_API int hsweep_default_opts(hsweep_opts* o);
+
+/*
+ * Assemble A for velocity c at angular frequency omega (Eq. sigma, Eq. helmd; PML of
+ * width eta = pml_width * h on all four sides) and run the setup sweep of
+ * Algorithm 2.5: for m = 1..n, S~_m from T~_{m-1} (hdiagmul + hsub), T~_m = hinv(S~_m).
+ * Off-diagonal blocks keep the singular values above eps_H times the block's largest
+ * one (at most r_max of them); eps_H = 0 keeps every one up to r_max.
+ *   c_dev      device, n*n doubles, node layout as above; every value finite and > 0
+ *   omega      > 0;  n >= 3;  0 <= pml_width < n/2;  eps_H >= 0
+ *   opt        NULL for the defaults
+ *   stream     a cudaStream_t (NULL = the legacy default stream)
+ *   out        receives the handle; *out = NULL on error (nothing leaked)
+ * Synchronises the stream; returns HSWEEP_ERR_NUMERIC if a leaf pivot vanished.
+ */
+HSWEEP_API int hsweep_setup(const double* c_dev, double omega, int n, int pml_width, double eps_H,
+                 const hsweep_opts* opt, void* stream, hsweep_t* out);
+
+/*
+ * Same as hsweep_setup but without the setup sweep: the H-factors are left empty
+ * (all ranks 0, zero leaves) for hsweep_import_layer.
+ */
+HSWEEP_API int hsweep_create(const double* c_dev, double omega, int n, int pml_width, double eps_H,
+                  const hsweep_opts* opt, void* stream, hsweep_t* out);
+
+/*
+ * z = M r, the approximate inverse of Algorithm 2.6 (forward sweep, reuse of
+ * T~_m u_m, backward sweep), for nrhs vectors at once.
+ *   r, z  device [nrhs][N]; r is not modified; r and z must not overlap.
+ * Stream-ordered; returns after enqueue.
+ */
+HSWEEP_API int hsweep_apply(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs);
+
+/* y = A x with the 5-point matrix of Eq. helmd (complex128).  x, y device [nrhs][N],
+   must not overlap.  Stream-ordered. */
+HSWEEP_API int hsweep_matvec(hsweep_t h, const hsw_c128* x, hsw_c128* y, int nrhs);
+
+/*
+ * Solve A u = f for nrhs right-hand sides by GMRES on M A u = M f (Section 2.4),
+ * unrestarted, x0 = u on entry (pass zeros for the default start).  Each RHS stops
+ * when ||M (f - A u)|| <= tol ||M f||.  In HSWEEP_MIXED the preconditioned solve is
+ * wrapped in FP64 iterative refinement on the true residual f - A u until
+ * ||f - A u|| <= tol_true ||f|| with tol_true = tol (at most refine_max steps).
+ *   f, u        device [nrhs][N]
+ *   iters_out   host int[nrhs] or NULL: Arnoldi steps taken (summed over refinement)
+ *   relres_out  host double[nrhs] or NULL: final ||f - A u|| / ||f|| (FP64)
+ * Synchronises.  HSWEEP_ERR_NOT_CONVERGED if any RHS missed tol (u holds the best
+ * iterate).
+ */
+HSWEEP_API int hsweep_solve(hsweep_t h, const hsw_c128* f, hsw_c128* u, int nrhs, double tol,
+                 int* iters_out, double* relres_out);
+
+/*
+ * Misfit J = 1/2 sum_s ||R u_s - d_s||^2 with A u_s = f_s, and its gradient with
+ * respect to the velocity c at the handle's c.  R samples the nodes rec_idx.
+ * Adjoint: A is complex symmetric (A^t = A), so A^H lambda = b is solved as
+ * lambda = conj(A^{-1} conj(b)) with the same factorisation;
+ * dJ/dc_i = -2 omega^2 c_i^{-3} sum_s Re(conj(lambda_{s,i}) u_{s,i} / (s1 s2)_i).
+ *   f       device [nsrc][N]
+ *   rec_idx device int[nrec], node offsets in [0, N)
+ *   d       device [nsrc][nrec]
+ *   grad    device double[N] (output)
+ *   misfit_out host double (output, may be NULL)
+ *   tol     GMRES tolerance of the forward and adjoint solves
+ * Synchronises.
+ */
+HSWEEP_API int hsweep_grad(hsweep_t h, const hsw_c128* f, int nsrc, const int* rec_idx, int nrec,
+                const hsw_c128* d, double* grad, double* misfit_out, double tol);
+
+/* Last device-side error code (an HSWEEP_ERR_* value, 0 if none) and the layer
+   (0-based row m) where it was raised, or -1.  Synchronises. */
+HSWEEP_API int hsweep_status(hsweep_t h, int* layer_out);
+
+/* Sizes of the handle: fills out[0..7] with n, tree depth L, leaf, r_max,
+   precision, number of leaves, total stored factor entries (all layers, actual
+   ranks) and bytes per stored entry.  Synchronises. */
+HSWEEP_API int hsweep_info(hsweep_t h, long long* out8);
+
+/*
+ * Ranks of T~_m (0-based layer m): ranks_out host int[2^(L+1)], entry v (heap order,
+ * root = 1, children of v are 2v and 2v+1) is the rank of the factorised block whose
+ * left factor sits on node v; entries 0 and 1 are 0.  Synchronises.
+ */
+HSWEEP_API int hsweep_layer_ranks(hsweep_t h, int m, int* ranks_out);
+
+/*
+ * Copy T~_m (0-based layer m) to or from HOST memory, in complex128, in the layout
+ * used on the device (weakly admissible, symmetric storage):
+ *   leaves  [n_leaves][leaf][leaf], column-major within a leaf (entry (a, b) at
+ *           b*leaf + a), zero-padded beyond the leaf's size;
+ *   factors for every non-root node v = 2 .. 2^(L+1)-1 in heap order, F_v of size
+ *           n_v x r_max column-major (entry (i, k) at k*n_v + i), where n_v is the
+ *           node's size and only the first ranks[v] columns are meaningful.  For
+ *           siblings a = 2t, b = 2t+1 the off-diagonal blocks are
+ *           T(a, b) = F_a F_b^t and T(b, a) = F_b F_a^t; ranks[a] = ranks[b].
+ *   ranks   host int[2^(L+1)] as in hsweep_layer_ranks.
+ * Buffer sizes: n_leaves*leaf*leaf and sum_v n_v*r_max = n*L*r_max entries.
+ * Import converts to the handle's storage precision.  Synchronises.
+ */
+HSWEEP_API int hsweep_export_layer(hsweep_t h, int m, hsw_c128* leaves, hsw_c128* factors, int* ranks);
+HSWEEP_API int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, const hsw_c128* factors,
+                        const int* ranks);
+
+/* Release every resource of the handle (NULL is allowed). */
+HSWEEP_API void hsweep_free(hsweep_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSWEEP_H */

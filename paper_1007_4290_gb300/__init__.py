@@ -1,0 +1,256 @@
+"""Python binding of libhsweep (include/hsweep.h): the sweeping preconditioner for the
+2D Helmholtz equation with H-matrix Schur complements, on one GB300 GPU.
+
+The functions below carry the C-ABI names and only marshal arguments (torch CUDA
+tensors -> device pointers, the current torch stream -> cudaStream_t).  Every step of
+the method runs in the CUDA kernels of libhsweep.so; there is no CPU fallback: if the
+library is missing the import of this module fails.
+
+Vectors are torch.complex128 CUDA tensors of shape (nrhs, n*n) (or (n*n,) for one),
+node (i, j) at (j-1)*n + (i-1), row by row with x1 fastest (Section 2.1).
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsweep.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_NOT_CONVERGED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NUMERIC",
+                -5: "ERR_NOT_CONVERGED", -6: "ERR_TIMEOUT"}
+
+EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_apply", "hsweep_matvec",
+            "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
+            "hsweep_export_layer", "hsweep_import_layer", "hsweep_free"]
+
+
+class hsweep_opts(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int), ("r_max", ctypes.c_int), ("precision", ctypes.c_int),
+                ("pml_C", ctypes.c_double), ("pml_form", ctypes.c_int), ("gmres_max_it", ctypes.c_int),
+                ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int)]
+
+
+class HSweepError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s failed: %s (%d)" % (where, STATUS_NAMES.get(code, "?"), code))
+        self.code = code
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libhsweep.so not built: run paper_1007_4290_gb300/build.py "
+                          "(or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "hsweep_default_opts": (I, [ctypes.POINTER(hsweep_opts)]),
+        "hsweep_setup": (I, [P, D, I, I, D, ctypes.POINTER(hsweep_opts), P, ctypes.POINTER(P)]),
+        "hsweep_create": (I, [P, D, I, I, D, ctypes.POINTER(hsweep_opts), P, ctypes.POINTER(P)]),
+        "hsweep_apply": (I, [P, P, P, I]),
+        "hsweep_matvec": (I, [P, P, P, I]),
+        "hsweep_solve": (I, [P, P, P, I, D, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "hsweep_grad": (I, [P, P, I, P, I, P, P, ctypes.POINTER(D), D]),
+        "hsweep_status": (I, [P, ctypes.POINTER(I)]),
+        "hsweep_info": (I, [P, ctypes.POINTER(LL)]),
+        "hsweep_layer_ranks": (I, [P, I, ctypes.POINTER(I)]),
+        "hsweep_export_layer": (I, [P, I, P, P, ctypes.POINTER(I)]),
+        "hsweep_import_layer": (I, [P, I, P, P, ctypes.POINTER(I)]),
+        "hsweep_free": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(code, where):
+    if code != OK:
+        raise HSweepError(code, where)
+
+
+def _ptr(t, dtype):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor of dtype %s" % dtype)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_opts(**kw):
+    o = hsweep_opts()
+    _check(_lib.hsweep_default_opts(ctypes.byref(o)), "hsweep_default_opts")
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """An hsweep handle; owns the factorisation.  Free with .free() (or on GC)."""
+
+    def __init__(self, raw, n):
+        self._h = raw
+        self.n = n
+        self.N = n * n
+
+    @property
+    def raw(self):
+        if self._h is None:
+            raise RuntimeError("handle already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            _lib.hsweep_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        out = (ctypes.c_longlong * 8)()
+        _check(_lib.hsweep_info(self.raw, out), "hsweep_info")
+        keys = ["n", "L", "leaf", "r_max", "precision", "nleaves", "entries", "bytes_per_entry"]
+        return dict(zip(keys, list(out)))
+
+    def status(self):
+        layer = ctypes.c_int(-1)
+        code = _lib.hsweep_status(self.raw, ctypes.byref(layer))
+        return code, layer.value
+
+    def layer_ranks(self, m):
+        L = self.info()["L"]
+        out = (ctypes.c_int * (1 << (L + 1)))()
+        _check(_lib.hsweep_layer_ranks(self.raw, m, out), "hsweep_layer_ranks")
+        return list(out)
+
+    # -- compute ------------------------------------------------------------------------
+    def apply(self, r, z=None):
+        """z = M r (Algorithm 2.6)."""
+        r2 = r.reshape(-1, self.N)
+        if z is None:
+            z = torch.empty_like(r2)
+        _check(_lib.hsweep_apply(self.raw, _ptr(r2, torch.complex128), _ptr(z, torch.complex128),
+                                 r2.shape[0]), "hsweep_apply")
+        return z.reshape(r.shape)
+
+    def matvec(self, x, y=None):
+        """y = A x (Eq. helmd)."""
+        x2 = x.reshape(-1, self.N)
+        if y is None:
+            y = torch.empty_like(x2)
+        _check(_lib.hsweep_matvec(self.raw, _ptr(x2, torch.complex128), _ptr(y, torch.complex128),
+                                  x2.shape[0]), "hsweep_matvec")
+        return y.reshape(x.shape)
+
+    def solve(self, f, tol, u=None, check=True):
+        """GMRES on M A u = M f; returns (u, iterations per RHS, true relative residuals)."""
+        f2 = f.reshape(-1, self.N)
+        nrhs = f2.shape[0]
+        if u is None:
+            u = torch.zeros_like(f2)
+        it = (ctypes.c_int * nrhs)()
+        rr = (ctypes.c_double * nrhs)()
+        code = _lib.hsweep_solve(self.raw, _ptr(f2, torch.complex128), _ptr(u, torch.complex128), nrhs,
+                                 float(tol), it, rr)
+        if check and code not in (OK,):
+            raise HSweepError(code, "hsweep_solve")
+        return u.reshape(f.shape), list(it), list(rr)
+
+    def grad(self, f, rec_idx, d, tol):
+        """Misfit and its gradient with respect to c: returns (J, grad (n*n,) float64)."""
+        f2 = f.reshape(-1, self.N)
+        g = torch.empty(self.N, dtype=torch.float64, device=f.device)
+        J = ctypes.c_double(0.0)
+        rec = rec_idx.to(device=f.device, dtype=torch.int32).contiguous()
+        d2 = d.reshape(f2.shape[0], -1).contiguous()
+        _check(_lib.hsweep_grad(self.raw, _ptr(f2, torch.complex128), f2.shape[0], _ptr(rec, torch.int32),
+                                rec.numel(), _ptr(d2, torch.complex128), _ptr(g, torch.float64),
+                                ctypes.byref(J), float(tol)), "hsweep_grad")
+        return J.value, g
+
+    # -- layer I/O (host, complex128) ---------------------------------------------------
+    def _layer_sizes(self):
+        inf = self.info()
+        L, leaf, r_max = inf["L"], inf["leaf"], inf["r_max"]
+        return (1 << L) * leaf * leaf, self.n * L * r_max, 1 << (L + 1)
+
+    def export_layer(self, m):
+        import numpy as np
+        nl, nf, nn = self._layer_sizes()
+        leaves = np.zeros(nl, np.complex128)
+        fac = np.zeros(nf, np.complex128)
+        ranks = (ctypes.c_int * nn)()
+        _check(_lib.hsweep_export_layer(self.raw, m, leaves.ctypes.data_as(ctypes.c_void_p),
+                                        fac.ctypes.data_as(ctypes.c_void_p), ranks), "hsweep_export_layer")
+        return leaves, fac, np.array(list(ranks), dtype=np.int32)
+
+    def import_layer(self, m, leaves, fac, ranks):
+        import numpy as np
+        nl, nf, nn = self._layer_sizes()
+        leaves = np.ascontiguousarray(leaves, np.complex128)
+        fac = np.ascontiguousarray(fac, np.complex128)
+        assert leaves.size == nl and fac.size == nf and len(ranks) == nn
+        rk = (ctypes.c_int * nn)(*[int(x) for x in ranks])
+        _check(_lib.hsweep_import_layer(self.raw, m, leaves.ctypes.data_as(ctypes.c_void_p),
+                                        fac.ctypes.data_as(ctypes.c_void_p), rk), "hsweep_import_layer")
+
+
+def _make(fn, c, omega, pml_width, eps_H, opts, name):
+    if not (c.is_cuda and c.dtype == torch.float64 and c.dim() == 2 and c.shape[0] == c.shape[1]):
+        raise ValueError("c must be an (n, n) float64 CUDA tensor")
+    c = c.contiguous()
+    n = c.shape[0]
+    raw = ctypes.c_void_p()
+    o = opts if opts is not None else default_opts()
+    _check(fn(ctypes.c_void_p(c.data_ptr()), float(omega), n, int(pml_width), float(eps_H), ctypes.byref(o),
+              _stream(), ctypes.byref(raw)), name)
+    return Handle(raw, n)
+
+
+def hsweep_setup(c, omega, pml_width, eps_H, opts=None):
+    """Assemble A and run the setup sweep of Algorithm 2.5 on the GPU."""
+    return _make(_lib.hsweep_setup, c, omega, pml_width, eps_H, opts, "hsweep_setup")
+
+
+def hsweep_create(c, omega, pml_width, eps_H, opts=None):
+    """Assemble A only (empty factors, for import_layer)."""
+    return _make(_lib.hsweep_create, c, omega, pml_width, eps_H, opts, "hsweep_create")
+
+
+def hsweep_apply(h, r, z=None):
+    return h.apply(r, z)
+
+
+def hsweep_matvec(h, x, y=None):
+    return h.matvec(x, y)
+
+
+def hsweep_solve(h, f, tol, u=None, check=True):
+    return h.solve(f, tol, u, check)
+
+
+def hsweep_grad(h, f, rec_idx, d, tol):
+    return h.grad(f, rec_idx, d, tol)
+
+
+def hsweep_status(h):
+    return h.status()
+
+
+def hsweep_free(h):
+    h.free()

@@ -1,0 +1,92 @@
+// Internal state of an hsweep handle, shared by the translation units of the library.
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+// Cluster tree of one layer (Section 2.3): heap-indexed nodes, root = 1, children of v
+// are 2v and 2v+1; a node [lo, lo+sz) of size s splits into ceil(s/2) and floor(s/2)
+// rows; all leaves sit at depth L, the smallest L with ceil(n / 2^L) <= leaf.
+struct Tree {
+  int n = 0, L = 0, leaf = 0, nnodes = 0, nleaves = 0;
+  std::vector<int> lo, sz;
+  void build(int n_, int leaf_) {
+    n = n_; leaf = leaf_;
+    L = 0;
+    while ((n + (1 << L) - 1) / (1 << L) > leaf) ++L;
+    nnodes = 1 << (L + 1);
+    nleaves = 1 << L;
+    lo.assign(nnodes, 0); sz.assign(nnodes, 0);
+    lo[1] = 0; sz[1] = n;
+    for (int v = 1; v < nnodes / 2; ++v) {
+      int a = (sz[v] + 1) / 2;
+      lo[2 * v] = lo[v]; sz[2 * v] = a;
+      lo[2 * v + 1] = lo[v] + a; sz[2 * v + 1] = sz[v] - a;
+    }
+  }
+  // largest node size at depth d
+  int maxsz(int d) const { return (n + (1 << d) - 1) >> d; }
+};
+
+struct SetupWork;   // setup.cu
+struct KrylovWork;  // krylov.cu
+
+struct hsweep_s {
+  int n = 0, N = 0, pml_width = 0;
+  double omega = 0, h = 0, eps_H = 0;
+  hsweep_opts opt{};
+  Tree tree;
+  int L = 0, leaf = 0, nnodes = 0, nleaves = 0, r_max = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0, device = 0;
+
+  // factor store: layer m occupies [m * layer_stride, (m+1) * layer_stride) entries;
+  // leaves first (nleaves * leaf * leaf), then F_v (sz[v] x r_max, column-major) at off[v].
+  std::vector<long long> off;
+  long long layer_stride = 0, leaf_entries = 0;
+  int* d_lo = nullptr;
+  int* d_sz = nullptr;
+  long long* d_off = nullptr;
+  void* d_fac = nullptr;   // c64 (HSWEEP_MIXED) or c128 (HSWEEP_FP64)
+  int* d_rank = nullptr;   // [n][nnodes]
+
+  // discretisation (complex128): diag [n][n], east [n][n+1], north [n+1][n], s1s2 [n][n]
+  double* d_c = nullptr;
+  c128* d_diag = nullptr;
+  c128* d_east = nullptr;
+  c128* d_north = nullptr;
+  c128* d_s1s2 = nullptr;
+
+  int* d_status = nullptr;     // [2]
+  unsigned* d_bar = nullptr;   // grid barrier words [2]
+
+  // sweep workspace
+  void* d_wcache = nullptr;    // [cap][N] in storage precision
+  void* d_xch = nullptr;       // team exchange slots
+  long long wcache_cap = 0, xch_cap = 0;
+
+  SetupWork* sw = nullptr;
+  KrylovWork* kw = nullptr;
+
+  std::vector<void*> allocs;   // every device allocation owned by the handle
+
+  size_t fac_elem() const { return prec == HSWEEP_FP64 ? sizeof(c128) : sizeof(c64); }
+};
+
+// Device allocation owned by the handle; HSWEEP_ERR_OOM on failure.
+int hsw_alloc(hsweep_s* h, void** p, size_t bytes);
+void hsw_release(hsweep_s* h, void* p);
+
+// assemble.cu
+int hsw_assemble(hsweep_s* h, double pml_C, int pml_form);
+int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
+// apply.cu
+int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs);
+// setup.cu
+int hsw_factor(hsweep_s* h);
+void hsw_setup_free(hsweep_s* h);
+// krylov.cu
+int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* iters, double* relres);
+void hsw_krylov_free(hsweep_s* h);
+// grad.cu
+int hsw_grad(hsweep_s* h, const c128* f, int nsrc, const int* rec, int nrec, const c128* d,
+             double* grad, double* misfit, double tol);

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point include/hsweep.h
+declares (no GPU needed: nothing here calls into the device)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "hsweep.h")).read()
+    return sorted(set(re.findall(r"HSWEEP_API\s+(?:int|void)\s+(hsweep_\w+)\s*\(", txt)))
+
+
+def _lib_path():
+    import __graft_entry__ as g
+    b = g._build_module()
+    if not os.path.exists(b.LIB):
+        b.build()
+    return b.LIB
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("hsweep_setup", "hsweep_apply", "hsweep_solve", "hsweep_grad",
+                     "hsweep_status", "hsweep_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_lib_path())
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_python_binding_lists_the_same_names():
+    _lib_path()
+    import paper_1007_4290_gb300 as hs
+    assert sorted(hs.EXPORTED) == _declared()
+
+
+def test_default_opts_and_argument_checks_without_gpu():
+    _lib_path()
+    import paper_1007_4290_gb300 as hs
+    o = hs.default_opts()
+    assert (o.leaf, o.r_max, o.precision, o.pml_form) == (8, 48, hs.MIXED, 0)
+    assert abs(o.pml_C - 2 * 3.141592653589793) < 1e-15
+    # argument errors are reported before any device work
+    raw = ctypes.c_void_p()
+    rc = hs._lib.hsweep_setup(None, 1.0, 64, 8, 1e-6, None, None, ctypes.byref(raw))
+    assert rc == hs.ERR_ARG and not raw.value
+    bad = hs.default_opts(leaf=9)
+    rc = hs._lib.hsweep_setup(ctypes.c_void_p(16), 1.0, 64, 8, 1e-6, ctypes.byref(bad), None, ctypes.byref(raw))
+    assert rc == hs.ERR_ARG
+    rc = hs._lib.hsweep_setup(ctypes.c_void_p(16), 1.0, 64, 40, 1e-6, None, None, ctypes.byref(raw))
+    assert rc == hs.ERR_ARG
+    assert hs._lib.hsweep_apply(None, None, None, 1) == hs.ERR_ARG
+    hs._lib.hsweep_free(None)
