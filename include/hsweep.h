@@ -62,7 +62,7 @@ enum {
 
 typedef struct {
   int leaf;          /* maximum leaf size of the cluster tree, 2..8 (default 8) */
-  int r_max;         /* rank cap of every factorised block, 1..64 (default 48) */
+  int r_max;         /* rank cap of every factorised block, 1..56 (default 48) */
   int precision;     /* HSWEEP_FP64 or HSWEEP_MIXED (default HSWEEP_MIXED) */
   double pml_C;      /* PML constant C of Eq. sigma (default 2 pi) */
   int pml_form;      /* 0: sigma = (C/eta)((t-eta)/eta)^2 as in Eq. sigma (default);

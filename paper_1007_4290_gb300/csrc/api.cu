@@ -75,7 +75,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   hsweep_default_opts(&opt);
   if (opt_in) opt = *opt_in;
   if (!c_dev || !(omega > 0) || n < 3 || n > 32767 || pml_width < 0 || 2 * pml_width >= n ||
-      !(eps_H >= 0) || opt.leaf < 2 || opt.leaf > 8 || opt.r_max < 1 || opt.r_max > 64 ||
+      !(eps_H >= 0) || opt.leaf < 2 || opt.leaf > 8 || opt.r_max < 1 || opt.r_max > 56 ||
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
       opt.refine_max < 1 || opt.team < 0 || opt.groups < 0)
@@ -166,6 +166,7 @@ extern "C" int hsweep_setup(const double* c_dev, double omega, int n, int pml_wi
   if (rc == HSWEEP_OK) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = HSWEEP_ERR_CUDA;
   }
+  hsw_setup_free(h);   // the setup workspace is not needed once the factors are stored
   if (rc == HSWEEP_OK) {
     int st[2] = {0, -1};
     if (cudaMemcpy(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HSWEEP_ERR_CUDA;

@@ -47,6 +47,14 @@ template <typename R> __host__ __device__ __forceinline__ Cx<R> cinv(Cx<R> a) {
   return Cx<R>(a.re * s, -a.im * s);
 }
 
+// principal square root
+template <typename R> __host__ __device__ __forceinline__ Cx<R> csqrt(Cx<R> a) {
+  R r = sqrt(a.re * a.re + a.im * a.im);
+  R x = sqrt((r + a.re) * R(0.5));
+  R y = sqrt((r - a.re) * R(0.5));
+  return Cx<R>(x, a.im < 0 ? -y : y);
+}
+
 template <typename R> __device__ __forceinline__ Cx<R> shfl_xor(Cx<R> v, int off) {
   return Cx<R>(__shfl_xor_sync(0xffffffffu, v.re, off), __shfl_xor_sync(0xffffffffu, v.im, off));
 }

@@ -1,3 +1,844 @@
+// The setup sweep of Algorithm 2.5 on the GPU: for m = 1..n
+//   S~_m = A_mm - A_{m,m-1} T~_{m-1} A_{m-1,m}   (hdiagmul + hsub; Section 2.3)
+//   T~_m = hinv(S~_m)
+// with every matrix a weakly admissible H-matrix in symmetric storage (siblings a, b:
+// block (a, b) = F_a F_b^t, block (b, a) = F_b F_a^t; dense leaves).
+//
+// hinv is organised level by level, bottom-up, instead of the paper's depth-first
+// 2 x 2 recursion; both give the same inverse before truncation.  For a node t with
+// children a, b and S(a, b) = U V^t:
+//     S_t = diag(S_a, S_b) + P C P^t,  P = diag(U, V),  C = [[0, I], [I, 0]],
+// so by the Woodbury identity, with G_a = S_a^{-1} and G_b = S_b^{-1} already built,
+//     Y = diag(G_a U, G_b V),  M = [[U^t Y_a, I], [I, V^t Y_b]]^{-1},
+//     S_t^{-1} = diag(G_a, G_b) - Y M Y^t.
+// The new off-diagonal block is -Y_a M12 Y_b^t; the diagonal corrections -Y_a M11 Y_a^t
+// and -Y_b M22 Y_b^t are rank-k updates of every block below a and b ("hadd" with a
+// factorised term).  All nodes of one depth are processed by the same launches, and
+// every block that received columns is recompressed once per depth ("Matrix
+// addition": QR of both factors, SVD of the small core, truncation at eps_H relative to
+// the block's largest singular value, at most r_max terms).  QR is classical
+// Gram-Schmidt with re-orthogonalisation; the SVD is one-sided (Hestenes) Jacobi.
+// The leaf inverses are computed in FP64 with partial pivoting in both precisions.
+#include <algorithm>
+#include <utility>
 #include "handle.h"
-int hsw_factor(hsweep_s* h) { (void)h; return HSWEEP_ERR_ARG; }
-void hsw_setup_free(hsweep_s* h) { (void)h; }
+
+namespace {
+
+constexpr int kBlk = 256;
+
+template <typename R> struct Tiny;
+template <> struct Tiny<double> {
+  static constexpr double dep = 1e-13;    // Gram-Schmidt: dependent-column threshold
+  static constexpr double jac = 1e-15;    // Jacobi: orthogonality tolerance
+  static constexpr double neg = 1e-200;   // Jacobi: negligible column (normalised)
+};
+template <> struct Tiny<float> {
+  static constexpr float dep = 2e-6f;
+  static constexpr float jac = 1e-7f;
+  static constexpr float neg = 1e-30f;
+};
+
+template <typename R> __device__ __forceinline__ Cx<R> warp_sum(Cx<R> v) {
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
+template <typename R> __device__ __forceinline__ R warp_sum_r(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a real value (result broadcast to all threads).
+template <typename R> __device__ R block_sum(R v, R* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_r(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  R t = 0;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+struct Geo {          // tree and buffer geometry passed by value to every kernel
+  int n, L, leaf, nnodes, r_max, KCAP, WCAP;
+  const int* lo;
+  const int* sz;
+  const int* rowleaf;      // [n] leaf node of each row
+  const long long* sfo;    // S factor offsets (capacity KCAP per node)
+  const long long* gfo;    // G factor offsets (capacity WCAP per node)
+};
+
+__device__ __forceinline__ int depth_of(int v) { return 31 - __clz(v); }
+
+// ---------------------------------------------------------------------------------
+// S~_m: leaves A_mm[leaf] - D T_leaf D, factors [-D F_a, a e_last] / [D F_b, e_first].
+template <typename R>
+__global__ void schur_leaves(Geo g, int m, const c128* __restrict__ diag, const c128* __restrict__ east,
+                             const c128* __restrict__ north, const Cx<R>* __restrict__ Tprev,
+                             Cx<R>* __restrict__ S_leaf) {
+  const int lam = (1 << g.L) + blockIdx.x;
+  const int lo = g.lo[lam], s = g.sz[lam], lf = g.leaf;
+  for (int e = threadIdx.x; e < lf * lf; e += blockDim.x) {
+    const int a = e % lf, b = e / lf;     // column-major: entry (a, b) at b*leaf + a
+    Cx<R> v(0, 0);
+    if (a < s && b < s) {
+      const int i = lo + a, j = lo + b;
+      c128 av(0, 0);
+      if (a == b) av = diag[(long long)m * g.n + i];
+      else if (j == i + 1) av = east[(long long)m * (g.n + 1) + j];
+      else if (i == j + 1) av = east[(long long)m * (g.n + 1) + i];
+      v = cvt<R>(av);
+      if (Tprev) {
+        Cx<R> di = cvt<R>(north[(long long)m * g.n + i]), dj = cvt<R>(north[(long long)m * g.n + j]);
+        v -= di * (Tprev[(long long)blockIdx.x * lf * lf + e] * dj);
+      }
+    } else if (a == b) {
+      v = Cx<R>(1, 0);    // identity padding keeps the padded leaf invertible
+    }
+    S_leaf[(long long)blockIdx.x * lf * lf + e] = v;
+  }
+}
+
+template <typename R>
+__global__ void schur_factors(Geo g, int m, const c128* __restrict__ east, const c128* __restrict__ north,
+                              const Cx<R>* __restrict__ Tprev, const long long* __restrict__ toff,
+                              const int* __restrict__ trank, Cx<R>* __restrict__ S_F, int* __restrict__ S_rank) {
+  const int v = 2 + blockIdx.x;
+  const int lo = g.lo[v], s = g.sz[v];
+  const bool left = (v & 1) == 0;
+  const int r0 = Tprev ? trank[v] : 0;
+  const int k = r0 + 1;
+  Cx<R>* dst = S_F + g.sfo[v];
+  const int edge = g.lo[v | 1];     // the coupling edge joins rows edge-1 and edge
+  for (int e = threadIdx.x; e < s * k; e += blockDim.x) {
+    const int i = e % s, col = e / s;
+    Cx<R> val(0, 0);
+    if (col < r0) {
+      Cx<R> dv = cvt<R>(north[(long long)m * g.n + lo + i]);
+      val = dv * Tprev[toff[v] + (long long)col * s + i];
+      if (left) val = -val;
+    } else {
+      // the rank-one coupling a e_last e_first^t, split as sqrt(a) on both sides so
+      // that the two factors carry the same scale
+      const c128 ra = csqrt(east[(long long)m * (g.n + 1) + edge]);
+      if (left) { if (i == s - 1) val = cvt<R>(ra); }
+      else if (i == 0) val = cvt<R>(ra);
+    }
+    dst[(long long)col * s + i] = val;
+  }
+  if (threadIdx.x == 0) S_rank[v] = k;
+}
+
+// ---------------------------------------------------------------------------------
+// Leaf inverses, FP64 Gauss-Jordan with partial pivoting (one block per leaf).
+template <typename R>
+__global__ void leaf_inverse(Geo g, int m, const Cx<R>* __restrict__ S_leaf, Cx<R>* __restrict__ G_leaf,
+                             int* status) {
+  __shared__ c128 A[8][16];
+  __shared__ c128 colk[8];
+  __shared__ int piv;
+  const int lf = g.leaf;
+  const Cx<R>* src = S_leaf + (long long)blockIdx.x * lf * lf;
+  for (int e = threadIdx.x; e < lf * 2 * lf; e += blockDim.x) {
+    int a = e / (2 * lf), b = e % (2 * lf);
+    A[a][b] = b < lf ? cvt<double>(src[b * lf + a]) : c128(a == b - lf ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  double scale = 0;
+  for (int a = 0; a < lf; ++a)
+    for (int b = 0; b < lf; ++b) scale = fmax(scale, sqrt(abs2(A[a][b])));
+  bool bad = false;
+  for (int k = 0; k < lf; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = abs2(A[k][k]);
+      for (int a = k + 1; a < lf; ++a)
+        if (abs2(A[a][k]) > best) { best = abs2(A[a][k]); p = a; }
+      piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k && threadIdx.x < 2 * lf) {
+      c128 t = A[k][threadIdx.x]; A[k][threadIdx.x] = A[p][threadIdx.x]; A[p][threadIdx.x] = t;
+    }
+    __syncthreads();
+    const c128 pv = A[k][k];
+    if (!(sqrt(abs2(pv)) > 1e-14 * scale)) { bad = true; break; }
+    const c128 ip = cinv(pv);
+    __syncthreads();
+    if (threadIdx.x < 2 * lf) A[k][threadIdx.x] = A[k][threadIdx.x] * ip;
+    if (threadIdx.x < lf) colk[threadIdx.x] = A[threadIdx.x][k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < lf * 2 * lf; e += blockDim.x) {
+      int a = e / (2 * lf), b = e % (2 * lf);
+      if (a != k) A[a][b] = A[a][b] - colk[a] * A[k][b];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) report_error(status, HSWEEP_ERR_NUMERIC, m);
+    return;
+  }
+  Cx<R>* dst = G_leaf + (long long)blockIdx.x * lf * lf;
+  for (int e = threadIdx.x; e < lf * lf; e += blockDim.x) {
+    int a = e % lf, b = e / lf;
+    dst[e] = cvt<R>(A[a][lf + b]);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Y_v = G_v X_v for every node v at depth d+1 (X_v = S factor of v, k_v columns):
+// an H-matrix times a tall-skinny block, as reductions (per node u below depth d+1:
+// Qr_u = F_u^t X restricted to u) followed by an expansion.
+template <typename R>
+__global__ void tsmm_reduce(Geo g, int d, const Cx<R>* __restrict__ G_F, const int* __restrict__ G_rank,
+                            const Cx<R>* __restrict__ S_F, const int* __restrict__ S_rank, Cx<R>* __restrict__ Qr) {
+  const int u = (1 << (d + 2)) + blockIdx.x;
+  const int du = depth_of(u);
+  const int nu = u >> (du - (d + 1));          // ancestor at depth d+1
+  const int ru = G_rank[u], k = S_rank[nu];
+  const int s = g.sz[u], ld_x = g.sz[nu], xo = g.lo[u] - g.lo[nu];
+  const Cx<R>* F = G_F + g.gfo[u];
+  const Cx<R>* X = S_F + g.sfo[nu];
+  Cx<R>* out = Qr + (long long)u * g.r_max * g.KCAP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int kr = warp; kr < ru; kr += nw) {
+    for (int c0 = 0; c0 < k; c0 += 8) {
+      Cx<R> acc[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc[t] = Cx<R>(0, 0);
+      for (int i = lane; i < s; i += 32) {
+        Cx<R> f = F[(long long)kr * s + i];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (c0 + t < k) cfma(acc[t], f, X[(long long)(c0 + t) * ld_x + xo + i]);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        Cx<R> v = warp_sum(acc[t]);
+        if (lane == 0 && c0 + t < k) out[kr * g.KCAP + c0 + t] = v;
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void tsmm_expand(Geo g, int d, const Cx<R>* __restrict__ G_leaf, const Cx<R>* __restrict__ G_F,
+                            const int* __restrict__ G_rank, const Cx<R>* __restrict__ S_F,
+                            const int* __restrict__ S_rank, const Cx<R>* __restrict__ Qr, Cx<R>* __restrict__ Y) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int col = blockIdx.y;
+  if (row >= g.n) return;
+  const int lam = g.rowleaf[row];
+  const int nu = lam >> (g.L - (d + 1));
+  const int k = S_rank[nu];
+  if (col >= k) return;
+  const int lo_nu = g.lo[nu], ld = g.sz[nu];
+  const Cx<R>* X = S_F + g.sfo[nu] + (long long)col * ld;
+  Cx<R> y(0, 0);
+  {
+    const int lf = g.leaf, a = row - g.lo[lam], s = g.sz[lam];
+    const Cx<R>* D = G_leaf + (long long)(lam - (1 << g.L)) * lf * lf;
+    for (int b = 0; b < s; ++b) cfma(y, D[b * lf + a], X[g.lo[lam] - lo_nu + b]);
+  }
+  for (int du = d + 2; du <= g.L; ++du) {
+    const int u = lam >> (g.L - du);
+    const int ru = G_rank[u];
+    const Cx<R>* F = G_F + g.gfo[u] + (row - g.lo[u]);
+    const Cx<R>* q = Qr + (long long)(u ^ 1) * g.r_max * g.KCAP + col;
+    const int s = g.sz[u];
+    for (int kr = 0; kr < ru; ++kr) cfma(y, F[(long long)kr * s], q[kr * g.KCAP]);
+  }
+  Y[(long long)lo_nu * g.KCAP + (long long)col * ld + (row - lo_nu)] = y;
+}
+
+// ---------------------------------------------------------------------------------
+// Woodbury core per node t at depth d: P = U^t Y_a, Q = V^t Y_b (k x k), then
+// M = [[P, I], [I, Q]]^{-1} by in-place Gauss-Jordan with partial pivoting.
+template <typename R>
+__global__ void core_dots(Geo g, int d, const Cx<R>* __restrict__ S_F, const int* __restrict__ S_rank,
+                          const Cx<R>* __restrict__ Y, Cx<R>* __restrict__ PQ) {
+  const int t = (1 << d) + blockIdx.x / 2;
+  const int side = blockIdx.x & 1;
+  const int v = 2 * t + side;
+  const int k = S_rank[v], s = g.sz[v];
+  const Cx<R>* U = S_F + g.sfo[v];
+  const Cx<R>* Yv = Y + (long long)g.lo[v] * g.KCAP;
+  Cx<R>* out = PQ + ((long long)(t - (1 << d)) * 2 + side) * g.KCAP * g.KCAP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = blockIdx.y * nw + warp; e < k * k; e += gridDim.y * nw) {
+    const int a = e / k, b = e % k;
+    Cx<R> acc(0, 0);
+    for (int i = lane; i < s; i += 32) cfma(acc, U[(long long)a * s + i], Yv[(long long)b * s + i]);
+    acc = warp_sum(acc);
+    if (lane == 0) out[a * g.KCAP + b] = acc;
+  }
+}
+
+template <typename R>
+__global__ void core_inverse(Geo g, int d, int m, const int* __restrict__ S_rank, const Cx<R>* __restrict__ PQ,
+                             Cx<R>* __restrict__ Mb, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int t = (1 << d) + blockIdx.x;
+  const int k = S_rank[2 * t];
+  const int n2 = 2 * k;
+  Cx<R>* A = reinterpret_cast<Cx<R>*>(sm);                 // n2 x n2, row-major
+  R* red = reinterpret_cast<R*>(A + n2 * n2);              // [32]
+  int* piv = reinterpret_cast<int*>(red + 32);             // [n2]
+  __shared__ int s_p;
+  __shared__ R s_best;
+  const Cx<R>* P = PQ + ((long long)(t - (1 << d)) * 2) * g.KCAP * g.KCAP;
+  const Cx<R>* Q = P + g.KCAP * g.KCAP;
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+    const int a = e / n2, b = e % n2;
+    Cx<R> v(0, 0);
+    if (a < k && b < k) v = P[a * g.KCAP + b];
+    else if (a >= k && b >= k) v = Q[(a - k) * g.KCAP + (b - k)];
+    else if (a < k && b == a + k) v = Cx<R>(1, 0);
+    else if (a >= k && b == a - k) v = Cx<R>(1, 0);
+    A[e] = v;
+  }
+  R mx = 0;
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) mx = fmax(mx, abs2(A[e]));
+  __syncthreads();
+  // block max
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = 0;
+    for (int i = 0; i < nw; ++i) mx = fmax(mx, red[i]);
+    __syncthreads();
+  }
+  const R tiny = (sizeof(R) == 8 ? R(1e-30) : R(1e-14)) * mx;   // on |pivot|^2
+  bool bad = false;
+  for (int kk = 0; kk < n2; ++kk) {
+    if (threadIdx.x == 0) {
+      int p = kk;
+      R best = abs2(A[kk * n2 + kk]);
+      for (int a = kk + 1; a < n2; ++a) {
+        R v = abs2(A[a * n2 + kk]);
+        if (v > best) { best = v; p = a; }
+      }
+      s_p = p;
+      s_best = best;
+      piv[kk] = p;
+    }
+    __syncthreads();
+    if (!(s_best > tiny)) { bad = true; break; }
+    const int p = s_p;
+    if (p != kk)
+      for (int b = threadIdx.x; b < n2; b += blockDim.x) {
+        Cx<R> tmp = A[kk * n2 + b]; A[kk * n2 + b] = A[p * n2 + b]; A[p * n2 + b] = tmp;
+      }
+    __syncthreads();
+    const Cx<R> ip = cinv(A[kk * n2 + kk]);
+    __syncthreads();
+    for (int b = threadIdx.x; b < n2; b += blockDim.x) {
+      Cx<R> v = (b == kk) ? Cx<R>(1, 0) : A[kk * n2 + b];
+      A[kk * n2 + b] = v * ip;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+      const int a = e / n2, b = e % n2;
+      if (a == kk) continue;
+      const Cx<R> f = A[a * n2 + kk];
+      if (b == kk) continue;
+      A[e] -= f * A[kk * n2 + b];
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < n2; a += blockDim.x)
+      if (a != kk) A[a * n2 + kk] = -(A[a * n2 + kk] * A[kk * n2 + kk]);
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) report_error(status, HSWEEP_ERR_NUMERIC, m);
+    return;
+  }
+  // undo the row interchanges as column interchanges, in reverse order
+  for (int kk = n2 - 1; kk >= 0; --kk) {
+    const int p = piv[kk];
+    if (p != kk)
+      for (int a = threadIdx.x; a < n2; a += blockDim.x) {
+        Cx<R> tmp = A[a * n2 + kk]; A[a * n2 + kk] = A[a * n2 + p]; A[a * n2 + p] = tmp;
+      }
+    __syncthreads();
+  }
+  Cx<R>* M = Mb + (long long)(t - (1 << d)) * 4 * g.KCAP * g.KCAP;
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+    const int a = e / n2, b = e % n2;
+    M[a * 2 * g.KCAP + b] = A[e];
+  }
+}
+
+// W_v = Y_v M_side (k x k block of M), and the new off-diagonal block at the parent:
+// F_a = -Y_a M12, F_b = Y_b.
+template <typename R>
+__global__ void woodbury_form(Geo g, int d, const int* __restrict__ S_rank, const Cx<R>* __restrict__ Y,
+                              const Cx<R>* __restrict__ Mb, Cx<R>* __restrict__ W, Cx<R>* __restrict__ G_F,
+                              int* __restrict__ G_rank) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int col = blockIdx.y;
+  if (row >= g.n) return;
+  const int v = g.rowleaf[row] >> (g.L - (d + 1));
+  const int t = v >> 1, side = v & 1;
+  const int k = S_rank[v];
+  if (col >= k) return;
+  const int s = g.sz[v], i = row - g.lo[v];
+  const Cx<R>* Yv = Y + (long long)g.lo[v] * g.KCAP;
+  const Cx<R>* M = Mb + (long long)(t - (1 << d)) * 4 * g.KCAP * g.KCAP;
+  const int ldm = 2 * g.KCAP;
+  const int off = side ? k : 0;
+  Cx<R> w(0, 0), nf(0, 0);
+  for (int j = 0; j < k; ++j) {
+    const Cx<R> y = Yv[(long long)j * s + i];
+    cfma(w, y, M[(off + j) * ldm + off + col]);          // M11 or M22
+    if (!side) cfma(nf, y, M[j * ldm + k + col]);         // M12
+  }
+  W[(long long)g.lo[v] * g.KCAP + (long long)col * s + i] = w;
+  Cx<R>* F = G_F + g.gfo[v];
+  F[(long long)col * s + i] = side ? Yv[(long long)col * s + i] : -nf;
+  if (i == 0 && col == 0) G_rank[v] = k;
+}
+
+// Append the rank-k correction to every node below depth d+1 and update the leaves
+// (a leaf at depth d+1 itself only gets the dense update; its factor slot holds the
+// new block written by woodbury_form).
+template <typename R>
+__global__ void woodbury_append(Geo g, int d, const int* __restrict__ S_rank, const Cx<R>* __restrict__ Y,
+                                const Cx<R>* __restrict__ W, Cx<R>* __restrict__ G_F, int* __restrict__ G_rank,
+                                Cx<R>* __restrict__ G_leaf) {
+  const int u = (1 << (d + 1)) + blockIdx.x;
+  const int du = depth_of(u);
+  const int nu = u >> (du - (d + 1));
+  const int k = S_rank[nu];
+  const bool append = du >= d + 2;
+  const int r0 = append ? G_rank[u] : 0;
+  const int s = g.sz[u], ld = g.sz[nu], xo = g.lo[u] - g.lo[nu];
+  const Cx<R>* Yv = Y + (long long)g.lo[nu] * g.KCAP;
+  const Cx<R>* Wv = W + (long long)g.lo[nu] * g.KCAP;
+  const bool left = (u & 1) == 0;
+  Cx<R>* F = G_F + g.gfo[u];
+  if (append)
+    for (int e = threadIdx.x; e < s * k; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      F[(long long)(r0 + j) * s + i] = left ? -Wv[(long long)j * ld + xo + i] : Yv[(long long)j * ld + xo + i];
+    }
+  if (du == g.L) {     // leaf: G_leaf -= W[leaf] Y[leaf]^t
+    const int lf = g.leaf;
+    Cx<R>* D = G_leaf + (long long)(u - (1 << g.L)) * lf * lf;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int a = e % s, b = e / s;
+      Cx<R> acc(0, 0);
+      for (int j = 0; j < k; ++j) cfma(acc, Wv[(long long)j * ld + xo + a], Yv[(long long)j * ld + xo + b]);
+      D[b * lf + a] -= acc;
+    }
+  }
+  __syncthreads();
+  if (append && threadIdx.x == 0) G_rank[u] = r0 + k;
+}
+
+// ---------------------------------------------------------------------------------
+// Recompression, step 1: Gram-Schmidt QR (twice-orthogonalised) of F_u in place; the
+// Q columns are compacted to the independent ones and R (qc x w) written out.
+template <typename R>
+__global__ void qr_cgs2(Geo g, int d, Cx<R>* __restrict__ G_F, const int* __restrict__ G_rank,
+                        Cx<R>* __restrict__ Rb, int* __restrict__ qcols) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int u = (1 << (d + 1)) + blockIdx.x;
+  const int s = g.sz[u], w = G_rank[u];
+  Cx<R>* F = G_F + g.gfo[u];
+  Cx<R>* Rm = Rb + (long long)u * g.WCAP * g.WCAP;      // row-major qc x w, ld WCAP
+  Cx<R>* v = reinterpret_cast<Cx<R>*>(sm);                // [s]
+  Cx<R>* c = v + s;                                        // [WCAP]
+  R* red = reinterpret_cast<R*>(c + g.WCAP);               // [32]
+  __shared__ int s_qc;
+  if (threadIdx.x == 0) s_qc = 0;
+  for (int e = threadIdx.x; e < g.WCAP * w; e += blockDim.x) Rm[(e / w) * g.WCAP + e % w] = Cx<R>(0, 0);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < w; ++j) {
+    const int qc = s_qc;
+    R nrm0 = 0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      v[i] = F[(long long)j * s + i];
+      nrm0 += abs2(v[i]);
+    }
+    nrm0 = block_sum(nrm0, red);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int l = warp; l < qc; l += nw) {
+        Cx<R> acc(0, 0);
+        for (int i = lane; i < s; i += 32) cfma_conj(acc, F[(long long)l * s + i], v[i]);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+          c[l] = acc;
+          Rm[l * g.WCAP + j] += acc;
+        }
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        Cx<R> acc = v[i];
+        for (int l = 0; l < qc; ++l) acc -= F[(long long)l * s + i] * c[l];
+        v[i] = acc;
+      }
+      __syncthreads();
+    }
+    R nr = 0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) nr += abs2(v[i]);
+    nr = block_sum(nr, red);
+    if (nr > Tiny<R>::dep * Tiny<R>::dep * nrm0 && nr > 0) {
+      const R sn = sqrt(nr), is = R(1) / sn;
+      for (int i = threadIdx.x; i < s; i += blockDim.x) F[(long long)qc * s + i] = is * v[i];
+      if (threadIdx.x == 0) {
+        Rm[qc * g.WCAP + j] = Cx<R>(sn, 0);
+        s_qc = qc + 1;
+      }
+    } else if (threadIdx.x == 0) {
+      // dependent column: its projections were accumulated into R; drop the remainder
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) qcols[u] = s_qc;
+}
+
+// Recompression, step 2: for every sibling pair (a, b), C = R_a R_b^t (qa x qb), one-sided
+// Jacobi C W = P Sigma, truncation, and the small transforms
+//   T_a = (P Sigma)[:, kept] (qa x k'),  T_b = conj(W)[:, kept] (qb x k').
+template <typename R>
+__global__ void svd_jacobi(Geo g, int d, double eps, const Cx<R>* __restrict__ Rb, const int* __restrict__ qcols,
+                           const int* __restrict__ G_rank, Cx<R>* __restrict__ Wb, Cx<R>* __restrict__ Tx,
+                           int* __restrict__ newrank) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int t = (1 << d) + blockIdx.x;
+  const int a = 2 * t, b = 2 * t + 1;
+  const int qa = qcols[a], qb = qcols[b], w = G_rank[a];
+  Cx<R>* C = reinterpret_cast<Cx<R>*>(sm);          // column-major qa x qb (ld qa)
+  R* sig = reinterpret_cast<R*>(C + (size_t)qa * qb);   // [qb]
+  int* order = reinterpret_cast<int*>(sig + qb + 1);    // [qb]
+  __shared__ int s_rot, s_keep;
+  __shared__ R s_scale;
+  Cx<R>* Wm = Wb + (long long)t * g.WCAP * g.WCAP;   // column-major qb x qb (ld WCAP)
+  const Cx<R>* Ra = Rb + (long long)a * g.WCAP * g.WCAP;
+  const Cx<R>* Rbm = Rb + (long long)b * g.WCAP * g.WCAP;
+  if (qa == 0 || qb == 0) {
+    if (threadIdx.x == 0) { newrank[a] = 0; newrank[b] = 0; }
+    return;
+  }
+  for (int e = threadIdx.x; e < qa * qb; e += blockDim.x) {
+    const int i = e % qa, j = e / qa;
+    Cx<R> acc(0, 0);
+    for (int l = 0; l < w; ++l) cfma(acc, Ra[i * g.WCAP + l], Rbm[j * g.WCAP + l]);
+    C[e] = acc;
+  }
+  for (int e = threadIdx.x; e < qb * qb; e += blockDim.x) {
+    const int i = e % qb, j = e / qb;
+    Wm[(long long)j * g.WCAP + i] = Cx<R>(i == j ? 1 : 0, 0);
+  }
+  __syncthreads();
+  // normalise by the largest column norm
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < qb; j += nw) {
+    R acc = 0;
+    for (int i = lane; i < qa; i += 32) acc += abs2(C[(long long)j * qa + i]);
+    acc = warp_sum_r(acc);
+    if (lane == 0) sig[j] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R mx = 0;
+    for (int j = 0; j < qb; ++j) mx = fmax(mx, sig[j]);
+    s_scale = sqrt(mx);
+  }
+  __syncthreads();
+  const R scale = s_scale;
+  if (!(scale > 0)) {
+    if (threadIdx.x == 0) { newrank[a] = 0; newrank[b] = 0; }
+    return;
+  }
+  const R iscale = R(1) / scale;
+  for (int e = threadIdx.x; e < qa * qb; e += blockDim.x) C[e] = iscale * C[e];
+  __syncthreads();
+  const int me = qb + (qb & 1);               // even number of positions (one dummy if odd)
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < me - 1; ++round) {
+      for (int pr = warp; pr < me / 2; pr += nw) {
+        int p0 = pr, p1 = me - 1 - pr;
+        int ip = p0 == 0 ? 0 : ((p0 - 1 + round) % (me - 1)) + 1;
+        int iq = ((p1 - 1 + round) % (me - 1)) + 1;
+        if (ip >= qb || iq >= qb) continue;
+        if (ip > iq) { int tmp = ip; ip = iq; iq = tmp; }
+        Cx<R>* cp = C + (long long)ip * qa;
+        Cx<R>* cq = C + (long long)iq * qa;
+        R al = 0, be = 0;
+        Cx<R> ga(0, 0);
+        for (int i = lane; i < qa; i += 32) {
+          al += abs2(cp[i]); be += abs2(cq[i]); cfma_conj(ga, cp[i], cq[i]);
+        }
+        al = warp_sum_r(al); be = warp_sum_r(be); ga = warp_sum(ga);
+        const R ag = sqrt(abs2(ga));
+        if (al < Tiny<R>::neg || be < Tiny<R>::neg || !(ag > Tiny<R>::jac * sqrt(al) * sqrt(be))) continue;
+        if (lane == 0) s_rot = 1;
+        const Cx<R> e(ga.re / ag, ga.im / ag);
+        const R z = (be - al) / (R(2) * ag);
+        const R tt = fabs(z) < R(1e18) ? (z >= 0 ? R(1) : R(-1)) / (fabs(z) + sqrt(R(1) + z * z)) : R(0.5) / z;
+        const R cs = R(1) / sqrt(R(1) + tt * tt), sn = tt * cs;
+        const Cx<R> snc = sn * conj(e), sne = sn * e;
+        for (int i = lane; i < qa; i += 32) {
+          const Cx<R> x = cp[i], y = cq[i];
+          cp[i] = cs * x - snc * y;
+          cq[i] = sne * x + cs * y;
+        }
+        Cx<R>* wp = Wm + (long long)ip * g.WCAP;
+        Cx<R>* wq = Wm + (long long)iq * g.WCAP;
+        for (int i = lane; i < qb; i += 32) {
+          const Cx<R> x = wp[i], y = wq[i];
+          wp[i] = cs * x - snc * y;
+          wq[i] = sne * x + cs * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // singular values, ordering, truncation
+  for (int j = warp; j < qb; j += nw) {
+    R acc = 0;
+    for (int i = lane; i < qa; i += 32) acc += abs2(C[(long long)j * qa + i]);
+    acc = warp_sum_r(acc);
+    if (lane == 0) sig[j] = sqrt(acc);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < qb; j += blockDim.x) {
+    int rk = 0;
+    for (int l = 0; l < qb; ++l) rk += (sig[l] > sig[j] || (sig[l] == sig[j] && l < j)) ? 1 : 0;
+    order[rk] = j;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const R smax = sig[order[0]];
+    int keep = 0;
+    while (keep < qb && keep < g.r_max && smax > 0 && sig[order[keep]] > R(eps) * smax && sig[order[keep]] > 0) ++keep;
+    s_keep = keep;
+    newrank[a] = keep;
+    newrank[b] = keep;
+  }
+  __syncthreads();
+  const int keep = s_keep;
+  Cx<R>* Ta = Tx + (long long)a * g.WCAP * g.r_max;   // column-major (ld WCAP)
+  Cx<R>* Tb = Tx + (long long)b * g.WCAP * g.r_max;
+  // balanced split: T_a = P_j sigma_j^(1/2), T_b = conj(W_j) sigma_j^(1/2)
+  for (int e = threadIdx.x; e < qa * keep; e += blockDim.x) {
+    const int i = e % qa, j = e / qa;
+    const R f = sqrt(scale / sig[order[j]]);
+    Ta[(long long)j * g.WCAP + i] = f * C[(long long)order[j] * qa + i];
+  }
+  for (int e = threadIdx.x; e < qb * keep; e += blockDim.x) {
+    const int i = e % qb, j = e / qb;
+    const R f = sqrt(scale * sig[order[j]]);
+    Tb[(long long)j * g.WCAP + i] = f * conj(Wm[(long long)order[j] * g.WCAP + i]);
+  }
+}
+
+// Recompression, step 3: F'_u = Q_u T_u (written to the other factor buffer).
+template <typename R>
+__global__ void recompress_apply(Geo g, int d, const Cx<R>* __restrict__ Q, const int* __restrict__ qcols,
+                                 const Cx<R>* __restrict__ Tx, const int* __restrict__ newrank,
+                                 Cx<R>* __restrict__ Fout, int* __restrict__ G_rank) {
+  const int u = (1 << (d + 1)) + blockIdx.x;
+  const int s = g.sz[u], qc = qcols[u], kr = newrank[u];
+  const Cx<R>* Qu = Q + g.gfo[u];
+  const Cx<R>* T = Tx + (long long)u * g.WCAP * g.r_max;
+  Cx<R>* F = Fout + g.gfo[u];
+  for (int e = threadIdx.x; e < s * kr; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    Cx<R> acc(0, 0);
+    for (int l = 0; l < qc; ++l) cfma(acc, Qu[(long long)l * s + i], T[(long long)j * g.WCAP + l]);
+    F[(long long)j * s + i] = acc;
+  }
+  if (threadIdx.x == 0) G_rank[u] = kr;
+}
+
+// T~_m into the factor store (leaf padding zeroed, factors truncated to r_max columns).
+template <typename R>
+__global__ void store_layer(Geo g, const Cx<R>* __restrict__ G_leaf, const Cx<R>* __restrict__ G_F,
+                            const int* __restrict__ G_rank, Cx<R>* __restrict__ dst, const long long* __restrict__ off,
+                            int* __restrict__ rank_dst) {
+  const int v = blockIdx.x;   // 0: leaves, v >= 2: factors
+  if (v == 0) {
+    const int lf = g.leaf;
+    const long long tot = (long long)(1 << g.L) * lf * lf;
+    for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int lam = (1 << g.L) + (int)(e / (lf * lf));
+      const int r = (int)(e % (lf * lf));
+      const int a = r % lf, b = r / lf, s = g.sz[lam];
+      dst[e] = (a < s && b < s) ? G_leaf[e] : Cx<R>(0, 0);
+    }
+    if (threadIdx.x == 0) { rank_dst[0] = 0; rank_dst[1] = 0; }
+    return;
+  }
+  if (v < 2) return;
+  const int s = g.sz[v], r = G_rank[v];
+  const Cx<R>* F = G_F + g.gfo[v];
+  for (int e = threadIdx.x; e < s * r; e += blockDim.x) dst[off[v] + e] = F[e];
+  if (threadIdx.x == 0) rank_dst[v] = r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+struct SetupWork {
+  int KCAP = 0, WCAP = 0;
+  std::vector<long long> sfo, gfo;
+  std::vector<int> rowleaf;
+  long long* d_sfo = nullptr;
+  long long* d_gfo = nullptr;
+  int* d_rowleaf = nullptr;
+  void *S_leaf = nullptr, *S_F = nullptr, *G_leaf = nullptr, *G_F = nullptr, *G_F2 = nullptr;
+  void *Y = nullptr, *W = nullptr, *Qr = nullptr, *PQ = nullptr, *M = nullptr, *Rb = nullptr;
+  void *Wb = nullptr, *Tx = nullptr;
+  int *S_rank = nullptr, *G_rank = nullptr, *qcols = nullptr, *newrank = nullptr;
+};
+
+void hsw_setup_free(hsweep_s* h) {
+  if (!h->sw) return;
+  SetupWork* w = h->sw;
+  void* ptrs[] = {w->d_sfo, w->d_gfo, w->d_rowleaf, w->S_leaf, w->S_F, w->G_leaf, w->G_F, w->G_F2,
+                  w->Y, w->W, w->Qr, w->PQ, w->M, w->Rb, w->Wb, w->Tx, w->S_rank, w->G_rank,
+                  w->qcols, w->newrank};
+  for (void* p : ptrs) hsw_release(h, p);
+  delete w;
+  h->sw = nullptr;
+}
+
+static int setup_alloc(hsweep_s* h) {
+  SetupWork* w = new (std::nothrow) SetupWork();
+  if (!w) return HSWEEP_ERR_OOM;
+  h->sw = w;
+  const size_t es = h->fac_elem();
+  const int nn = h->nnodes;
+  w->KCAP = h->r_max + 1;
+  w->WCAP = h->r_max + w->KCAP;
+  w->sfo.assign(nn, 0);
+  w->gfo.assign(nn, 0);
+  long long so = 0, go = 0;
+  for (int v = 2; v < nn; ++v) {
+    w->sfo[v] = so; so += (long long)h->tree.sz[v] * w->KCAP;
+    w->gfo[v] = go; go += (long long)h->tree.sz[v] * w->WCAP;
+  }
+  w->rowleaf.assign(h->n, 0);
+  for (int lam = h->nleaves; lam < 2 * h->nleaves; ++lam)
+    for (int i = 0; i < h->tree.sz[lam]; ++i) w->rowleaf[h->tree.lo[lam] + i] = lam;
+  const long long lf2 = (long long)h->nleaves * h->leaf * h->leaf;
+  const long long ntau = std::max(1, h->nleaves / 2);
+  int rc;
+#define A(p, bytes) do { rc = hsw_alloc(h, (void**)&(p), (size_t)(bytes)); if (rc) return rc; } while (0)
+  A(w->d_sfo, nn * sizeof(long long));
+  A(w->d_gfo, nn * sizeof(long long));
+  A(w->d_rowleaf, h->n * sizeof(int));
+  A(w->S_leaf, lf2 * es);
+  A(w->G_leaf, lf2 * es);
+  A(w->S_F, std::max(so, 1LL) * es);
+  A(w->G_F, std::max(go, 1LL) * es);
+  A(w->G_F2, std::max(go, 1LL) * es);
+  A(w->Y, (long long)h->n * w->KCAP * es);
+  A(w->W, (long long)h->n * w->KCAP * es);
+  A(w->Qr, (long long)nn * h->r_max * w->KCAP * es);
+  A(w->PQ, ntau * 2 * w->KCAP * w->KCAP * es);
+  A(w->M, ntau * 4 * w->KCAP * w->KCAP * es);
+  A(w->Rb, (long long)nn * w->WCAP * w->WCAP * es);
+  A(w->Wb, (long long)nn * w->WCAP * w->WCAP * es);
+  A(w->Tx, (long long)nn * w->WCAP * h->r_max * es);
+  A(w->S_rank, nn * sizeof(int));
+  A(w->G_rank, nn * sizeof(int));
+  A(w->qcols, nn * sizeof(int));
+  A(w->newrank, nn * sizeof(int));
+#undef A
+  HSW_CUDA(cudaMemcpyAsync(w->d_sfo, w->sfo.data(), nn * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  HSW_CUDA(cudaMemcpyAsync(w->d_gfo, w->gfo.data(), nn * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  HSW_CUDA(cudaMemcpyAsync(w->d_rowleaf, w->rowleaf.data(), h->n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  HSW_CUDA(cudaMemsetAsync(w->S_rank, 0, nn * sizeof(int), h->stream));
+  return HSWEEP_OK;
+}
+
+template <typename R>
+static int factor_impl(hsweep_s* h) {
+  SetupWork* w = h->sw;
+  const size_t es = sizeof(Cx<R>);
+  Geo g;
+  g.n = h->n; g.L = h->L; g.leaf = h->leaf; g.nnodes = h->nnodes; g.r_max = h->r_max;
+  g.KCAP = w->KCAP; g.WCAP = w->WCAP;
+  g.lo = h->d_lo; g.sz = h->d_sz; g.rowleaf = w->d_rowleaf; g.sfo = w->d_sfo; g.gfo = w->d_gfo;
+  cudaStream_t st = h->stream;
+  Cx<R>* fac = reinterpret_cast<Cx<R>*>(h->d_fac);
+  Cx<R>* S_leaf = (Cx<R>*)w->S_leaf;
+  Cx<R>* S_F = (Cx<R>*)w->S_F;
+  Cx<R>* G_leaf = (Cx<R>*)w->G_leaf;
+  Cx<R>* G_F = (Cx<R>*)w->G_F;
+  Cx<R>* G_F2 = (Cx<R>*)w->G_F2;
+  Cx<R>* Y = (Cx<R>*)w->Y;
+  Cx<R>* Wv = (Cx<R>*)w->W;
+  Cx<R>* Qr = (Cx<R>*)w->Qr;
+  Cx<R>* PQ = (Cx<R>*)w->PQ;
+  Cx<R>* M = (Cx<R>*)w->M;
+  Cx<R>* Rb = (Cx<R>*)w->Rb;
+  Cx<R>* Wb = (Cx<R>*)w->Wb;
+  Cx<R>* Tx = (Cx<R>*)w->Tx;
+  const int L = h->L, nn = h->nnodes, KCAP = w->KCAP, WCAP = w->WCAP;
+  const size_t core_smem = (size_t)(2 * KCAP) * (2 * KCAP) * es + 32 * sizeof(R) + (2 * KCAP + 1) * sizeof(int) + 16;
+  const size_t qr_smem = (size_t)(h->tree.maxsz(1) + WCAP) * es + 32 * sizeof(R) + 16;
+  const size_t svd_smem = (size_t)WCAP * WCAP * es + (WCAP + 1) * (sizeof(R) + sizeof(int)) + 64;
+  HSW_CUDA(cudaFuncSetAttribute(core_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem));
+  HSW_CUDA(cudaFuncSetAttribute(qr_cgs2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem));
+  HSW_CUDA(cudaFuncSetAttribute(svd_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)svd_smem));
+  if (core_smem > 227 * 1024 || qr_smem > 227 * 1024 || svd_smem > 227 * 1024) return HSWEEP_ERR_ARG;
+
+  for (int m = 0; m < h->n; ++m) {
+    const Cx<R>* Tprev = m > 0 ? fac + (long long)(m - 1) * h->layer_stride : nullptr;
+    const int* rprev = m > 0 ? h->d_rank + (long long)(m - 1) * nn : nullptr;
+    schur_leaves<R><<<h->nleaves, 64, 0, st>>>(g, m, h->d_diag, h->d_east, h->d_north, Tprev, S_leaf);
+    if (nn > 2)
+      schur_factors<R><<<nn - 2, kBlk, 0, st>>>(g, m, h->d_east, h->d_north, Tprev, h->d_off, rprev, S_F,
+                                                 w->S_rank);
+    HSW_CUDA(cudaMemsetAsync(w->G_rank, 0, nn * sizeof(int), st));
+    leaf_inverse<R><<<h->nleaves, 128, 0, st>>>(g, m, S_leaf, G_leaf, h->d_status);
+    for (int d = L - 1; d >= 0; --d) {
+      const int n_below2 = (d + 2 <= L) ? (1 << (L + 1)) - (1 << (d + 2)) : 0;
+      const int n_below1 = (1 << (L + 1)) - (1 << (d + 1));
+      const int ntau_d = 1 << d;
+      if (n_below2 > 0)
+        tsmm_reduce<R><<<n_below2, kBlk, 0, st>>>(g, d, G_F, w->G_rank, S_F, w->S_rank, Qr);
+      tsmm_expand<R><<<dim3(div_up(h->n, 128), KCAP), 128, 0, st>>>(g, d, G_leaf, G_F, w->G_rank, S_F,
+                                                                     w->S_rank, Qr, Y);
+      core_dots<R><<<dim3(2 * ntau_d, 8), kBlk, 0, st>>>(g, d, S_F, w->S_rank, Y, PQ);
+      core_inverse<R><<<ntau_d, 512, core_smem, st>>>(g, d, m, w->S_rank, PQ, M, h->d_status);
+      woodbury_form<R><<<dim3(div_up(h->n, 128), KCAP), 128, 0, st>>>(g, d, w->S_rank, Y, M, Wv, G_F, w->G_rank);
+      woodbury_append<R><<<n_below1, kBlk, 0, st>>>(g, d, w->S_rank, Y, Wv, G_F, w->G_rank, G_leaf);
+      qr_cgs2<R><<<n_below1, kBlk, qr_smem, st>>>(g, d, G_F, w->G_rank, Rb, w->qcols);
+      svd_jacobi<R><<<n_below1 / 2, kBlk, svd_smem, st>>>(g, d, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx,
+                                                         w->newrank);
+      recompress_apply<R><<<n_below1, kBlk, 0, st>>>(g, d, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);
+      std::swap(G_F, G_F2);
+    }
+    store_layer<R><<<nn, kBlk, 0, st>>>(g, G_leaf, G_F, w->G_rank, fac + (long long)m * h->layer_stride,
+                                        h->d_off, h->d_rank + (long long)m * nn);
+    HSW_CUDA(cudaGetLastError());
+  }
+  w->G_F = G_F;
+  w->G_F2 = G_F2;
+  return HSWEEP_OK;
+}
+
+int hsw_factor(hsweep_s* h) {
+  if (!h->sw) {
+    int rc = setup_alloc(h);
+    if (rc) return rc;
+  }
+  if (h->prec == HSWEEP_FP64) return factor_impl<double>(h);
+  return factor_impl<float>(h);
+}
