@@ -1,3 +1,364 @@
+// GMRES on the left-preconditioned system M A u = M f (Section 2.4), batched over
+// right-hand sides, with FP64 Arnoldi (classical Gram-Schmidt, applied twice), Givens
+// rotations on the host, and an outer loop on the FP64 residual:
+//     r = f - A u,  z = M r,  stop when ||z|| <= tol ||M f||,
+//     otherwise GMRES on M A d = z (x0 = 0) and u += d.
+// In HSWEEP_FP64 a converged inner solve ends the loop (its residual estimate is the
+// FP64 one); in HSWEEP_MIXED, where M runs in complex64, every outer step re-checks
+// the FP64 residual (iterative refinement).
+#include <algorithm>
+#include <cmath>
+#include <complex>
 #include "handle.h"
-int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* iters, double* relres) { return HSWEEP_ERR_ARG; }
-void hsw_krylov_free(hsweep_s* h) { (void)h; }
+
+namespace {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs of partial sums per vector
+
+// partial[(s * nv + i) * B + b] = sum over block b's chunk of conj(V_i[s]) . w[s]
+__global__ void dots_kernel(const c128* const* __restrict__ V, int nv, const c128* __restrict__ w, long long N,
+                            c128* __restrict__ partial) {
+  const int s = blockIdx.y, B = gridDim.x;
+  const long long chunk = (N + B - 1) / B;
+  const long long beg = blockIdx.x * chunk, end = min(N, beg + chunk);
+  __shared__ c128 red[32];
+  const c128* ws = w + s * N;
+  for (int i = 0; i < nv; ++i) {
+    const c128* vs = V[i] + s * N;
+    c128 acc(0, 0);
+    for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) cfma_conj(acc, vs[p], ws[p]);
+    for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c128 t(0, 0);
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+      partial[((long long)s * nv + i) * B + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void reduce_partials(const c128* __restrict__ partial, int B, c128* __restrict__ out) {
+  const int idx = blockIdx.x;
+  __shared__ c128 red[32];
+  c128 acc(0, 0);
+  for (int b = threadIdx.x; b < B; b += blockDim.x) acc += partial[(long long)idx * B + b];
+  for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c128 t(0, 0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    out[idx] = t;
+  }
+}
+
+// y[s] += sign * sum_i coef[s * ldc + i] * V_i[s]
+__global__ void axpy_multi(const c128* const* __restrict__ V, int nv, const c128* __restrict__ coef, int ldc,
+                           double sign, c128* __restrict__ y, long long N) {
+  const int s = blockIdx.y;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    c128 acc = y[s * N + p];
+    for (int i = 0; i < nv; ++i) {
+      c128 cf = coef[(long long)s * ldc + i];
+      cfma(acc, sign * cf, V[i][s * N + p]);
+    }
+    y[s * N + p] = acc;
+  }
+}
+
+// v[s] = w[s] / nrm[s] (zero when nrm[s] = 0)
+__global__ void scale_kernel(const c128* __restrict__ w, const double* __restrict__ nrm, c128* __restrict__ v,
+                             long long N) {
+  const int s = blockIdx.y;
+  const double a = nrm[s] > 0 ? 1.0 / nrm[s] : 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    v[s * N + p] = a * w[s * N + p];
+}
+
+// r = f - y
+__global__ void sub_kernel(const c128* __restrict__ f, const c128* __restrict__ y, c128* __restrict__ r, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    r[p] = f[p] - y[p];
+}
+
+}  // namespace
+
+struct KrylovWork {
+  int nrhs_cap = 0;
+  std::vector<c128*> V;        // basis vectors, each [nrhs_cap][N]
+  c128** d_V = nullptr;        // device copy of the pointer table
+  int d_V_cap = 0;
+  c128 *r = nullptr, *z = nullptr, *w = nullptr, *t = nullptr, *d = nullptr;
+  c128* partial = nullptr;
+  c128* dots = nullptr;        // [nrhs][vmax]
+  c128* coef = nullptr;        // [nrhs][vmax]
+  double* nrm = nullptr;       // [nrhs]
+  int vmax = 0;
+};
+
+void hsw_krylov_free(hsweep_s* h) {
+  if (!h->kw) return;
+  KrylovWork* k = h->kw;
+  for (c128* p : k->V) hsw_release(h, p);
+  void* ptrs[] = {k->d_V, k->r, k->z, k->w, k->t, k->d, k->partial, k->dots, k->coef, k->nrm};
+  for (void* p : ptrs) hsw_release(h, p);
+  delete k;
+  h->kw = nullptr;
+}
+
+static int krylov_reserve(hsweep_s* h, int nrhs) {
+  const int vmax = h->opt.gmres_max_it + 1;
+  if (h->kw && h->kw->nrhs_cap >= nrhs) return HSWEEP_OK;
+  hsw_krylov_free(h);
+  KrylovWork* k = new (std::nothrow) KrylovWork();
+  if (!k) return HSWEEP_ERR_OOM;
+  h->kw = k;
+  k->nrhs_cap = nrhs;
+  k->vmax = vmax;
+  const size_t vb = (size_t)nrhs * h->N * sizeof(c128);
+  int rc;
+#define A(p, bytes) do { rc = hsw_alloc(h, (void**)&(p), (size_t)(bytes)); if (rc) return rc; } while (0)
+  A(k->d_V, vmax * sizeof(c128*));
+  A(k->r, vb); A(k->z, vb); A(k->w, vb); A(k->t, vb); A(k->d, vb);
+  A(k->partial, (size_t)nrhs * vmax * kRedBlocks * sizeof(c128));
+  A(k->dots, (size_t)nrhs * vmax * sizeof(c128));
+  A(k->coef, (size_t)nrhs * vmax * sizeof(c128));
+  A(k->nrm, (size_t)nrhs * sizeof(double));
+#undef A
+  return HSWEEP_OK;
+}
+
+// basis vector i (allocated on first use)
+static int basis(hsweep_s* h, int i, c128** out) {
+  KrylovWork* k = h->kw;
+  while ((int)k->V.size() <= i) {
+    c128* p = nullptr;
+    int rc = hsw_alloc(h, (void**)&p, (size_t)k->nrhs_cap * h->N * sizeof(c128));
+    if (rc) return rc;
+    k->V.push_back(p);
+  }
+  if (k->d_V_cap < (int)k->V.size()) {
+    HSW_CUDA(cudaMemcpyAsync(k->d_V, k->V.data(), k->V.size() * sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
+    k->d_V_cap = (int)k->V.size();
+  }
+  *out = k->V[i];
+  return HSWEEP_OK;
+}
+
+// dots[s * vmax + i] = <V_{first+i}[s], w[s]> for i < nv, copied to host hd (nrhs x nv)
+static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs, std::vector<std::complex<double>>& hd) {
+  KrylovWork* k = h->kw;
+  dots_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(k->d_V + first, nv, w, h->N, k->partial);
+  reduce_partials<<<nrhs * nv, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
+  HSW_CUDA(cudaGetLastError());
+  hd.resize((size_t)nrhs * nv);
+  HSW_CUDA(cudaMemcpyAsync(hd.data(), k->dots, (size_t)nrhs * nv * sizeof(c128), cudaMemcpyDeviceToHost, h->stream));
+  HSW_CUDA(cudaStreamSynchronize(h->stream));
+  return HSWEEP_OK;
+}
+
+// ||x[s]|| for every s, on the host
+static int norms(hsweep_s* h, const c128* x, int nrhs, std::vector<double>& out) {
+  KrylovWork* k = h->kw;
+  // use the pointer table slot after the basis for x
+  const c128* tbl[1] = {x};
+  c128** d_tmp = k->d_V + (k->vmax - 1);
+  (void)d_tmp;
+  static_assert(sizeof(c128*) == 8, "pointer size");
+  // a one-entry table lives in the coef buffer (it is not in use while norms run)
+  HSW_CUDA(cudaMemcpyAsync(k->coef, tbl, sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
+  dots_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->coef), 1, x,
+                                                               h->N, k->partial);
+  reduce_partials<<<nrhs, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
+  HSW_CUDA(cudaGetLastError());
+  std::vector<std::complex<double>> hd(nrhs);
+  HSW_CUDA(cudaMemcpyAsync(hd.data(), k->dots, nrhs * sizeof(c128), cudaMemcpyDeviceToHost, h->stream));
+  HSW_CUDA(cudaStreamSynchronize(h->stream));
+  out.resize(nrhs);
+  for (int s = 0; s < nrhs; ++s) out[s] = std::sqrt(std::max(0.0, hd[s].real()));
+  return HSWEEP_OK;
+}
+
+static dim3 vec_grid(hsweep_s* h, int nrhs) {
+  long long blocks = (h->N + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  return dim3((unsigned)blocks, nrhs);
+}
+
+// Inner GMRES on (M A) d = z, x0 = 0.  eta[s]: relative tolerance on ||z_s||; active[s]
+// marks the right-hand sides being solved.  Adds the Arnoldi steps to iters.
+static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<double>& znrm,
+                       const std::vector<double>& eta, std::vector<char>& active, c128* d, std::vector<int>& iters,
+                       std::vector<double>& est) {
+  KrylovWork* k = h->kw;
+  const int maxit = h->opt.gmres_max_it;
+  const long long N = h->N;
+  typedef std::complex<double> cd;
+  std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(maxit + 1) * maxit, cd(0)));
+  std::vector<std::vector<cd>> cs(nrhs, std::vector<cd>(maxit)), sn(nrhs, std::vector<cd>(maxit));
+  std::vector<std::vector<cd>> g(nrhs, std::vector<cd>(maxit + 1, cd(0)));
+  std::vector<int> ks(nrhs, 0);
+  std::vector<char> run(active);
+  for (int s = 0; s < nrhs; ++s) {
+    g[s][0] = cd(znrm[s], 0);
+    est[s] = 1.0;
+    if (!(znrm[s] > 0)) run[s] = 0;
+  }
+  c128* v0;
+  int rc = basis(h, 0, &v0);
+  if (rc) return rc;
+  {
+    std::vector<double> zn(znrm);
+    HSW_CUDA(cudaMemcpyAsync(k->nrm, zn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    scale_kernel<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
+  }
+  std::vector<cd> hd, hd2;
+  int j = 0;
+  for (; j < maxit; ++j) {
+    bool any = false;
+    for (int s = 0; s < nrhs; ++s) any |= run[s] != 0;
+    if (!any) break;
+    c128 *vj, *vn;
+    if ((rc = basis(h, j, &vj))) return rc;
+    if ((rc = basis(h, j + 1, &vn))) return rc;
+    // w = M (A v_j)
+    if ((rc = hsw_matvec(h, vj, k->t, nrhs))) return rc;
+    if ((rc = hsw_apply(h, k->t, k->w, nrhs))) return rc;
+    // classical Gram-Schmidt, twice
+    std::vector<cd> hcol((size_t)nrhs * (j + 1), cd(0));
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((rc = batched_dots(h, 0, j + 1, k->w, nrhs, hd))) return rc;
+      for (size_t e = 0; e < hd.size(); ++e) hcol[e] += hd[e];
+      HSW_CUDA(cudaMemcpyAsync(k->coef, hd.data(), hd.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
+      axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
+    }
+    std::vector<double> wn;
+    if ((rc = norms(h, k->w, nrhs, wn))) return rc;
+    HSW_CUDA(cudaMemcpyAsync(k->nrm, wn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    scale_kernel<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
+    for (int s = 0; s < nrhs; ++s) {
+      if (!run[s]) continue;
+      cd* Hs = H[s].data();
+      for (int i = 0; i <= j; ++i) Hs[i * maxit + j] = hcol[(size_t)s * (j + 1) + i];
+      Hs[(j + 1) * maxit + j] = cd(wn[s], 0);
+      for (int i = 0; i < j; ++i) {
+        cd a = Hs[i * maxit + j], b = Hs[(i + 1) * maxit + j];
+        Hs[i * maxit + j] = cs[s][i] * a + sn[s][i] * b;
+        Hs[(i + 1) * maxit + j] = -std::conj(sn[s][i]) * a + std::conj(cs[s][i]) * b;
+      }
+      cd a = Hs[j * maxit + j], b = Hs[(j + 1) * maxit + j];
+      double r = std::sqrt(std::norm(a) + std::norm(b));
+      cs[s][j] = r != 0 ? std::conj(a) / r : cd(1);
+      sn[s][j] = r != 0 ? std::conj(b) / r : cd(0);
+      Hs[j * maxit + j] = cd(r, 0);
+      Hs[(j + 1) * maxit + j] = 0;
+      g[s][j + 1] = -std::conj(sn[s][j]) * g[s][j];
+      g[s][j] = cs[s][j] * g[s][j];
+      ks[s] = j + 1;
+      iters[s] += 1;
+      est[s] = std::abs(g[s][j + 1]) / znrm[s];
+      if (est[s] <= eta[s] || wn[s] == 0.0 || r == 0.0) run[s] = 0;
+    }
+  }
+  // d = sum_i y_i v_i with H y = g (upper-triangular back substitution per RHS)
+  std::vector<cd> Y((size_t)nrhs * std::max(1, maxit), cd(0));
+  int kmax = 0;
+  for (int s = 0; s < nrhs; ++s) {
+    if (!active[s]) continue;
+    const int kk = ks[s];
+    kmax = std::max(kmax, kk);
+    cd* Hs = H[s].data();
+    for (int i = kk - 1; i >= 0; --i) {
+      cd acc = g[s][i];
+      for (int l = i + 1; l < kk; ++l) acc -= Hs[i * maxit + l] * Y[(size_t)s * maxit + l];
+      Y[(size_t)s * maxit + i] = Hs[i * maxit + i] != cd(0) ? acc / Hs[i * maxit + i] : cd(0);
+    }
+  }
+  HSW_CUDA(cudaMemsetAsync(d, 0, (size_t)nrhs * N * sizeof(c128), h->stream));
+  if (kmax > 0) {
+    std::vector<cd> Yc((size_t)nrhs * kmax, cd(0));
+    for (int s = 0; s < nrhs; ++s)
+      for (int i = 0; i < kmax; ++i) Yc[(size_t)s * kmax + i] = Y[(size_t)s * maxit + i];
+    HSW_CUDA(cudaMemcpyAsync(k->coef, Yc.data(), Yc.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
+    axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
+    HSW_CUDA(cudaGetLastError());
+  }
+  HSW_CUDA(cudaStreamSynchronize(h->stream));
+  return HSWEEP_OK;
+}
+
+int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* iters_out, double* relres_out) {
+  int rc = krylov_reserve(h, nrhs);
+  if (rc) return rc;
+  KrylovWork* k = h->kw;
+  const long long N = h->N;
+  const bool mixed = h->prec == HSWEEP_MIXED;
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> Mfn, fn, zn, est(nrhs, 1.0);
+  // ||M f|| (the reference of the stopping test) and ||f||
+  if ((rc = hsw_apply(h, f, k->z, nrhs))) return rc;
+  if ((rc = norms(h, k->z, nrhs, Mfn))) return rc;
+  if ((rc = norms(h, f, nrhs, fn))) return rc;
+  std::vector<char> done(nrhs, 0);
+  const int outer_max = h->opt.refine_max;
+  bool all_done = false;
+  for (int outer = 0; outer < outer_max && !all_done; ++outer) {
+    // r = f - A u, z = M r
+    if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
+    sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
+    if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
+    if ((rc = norms(h, k->z, nrhs, zn))) return rc;
+    std::vector<char> active(nrhs, 0);
+    std::vector<double> eta(nrhs, 0.0);
+    all_done = true;
+    for (int s = 0; s < nrhs; ++s) {
+      if (!(zn[s] > tol * Mfn[s])) { done[s] = 1; continue; }
+      done[s] = 0;
+      active[s] = 1;
+      all_done = false;
+      const double need = tol * Mfn[s] / zn[s];
+      eta[s] = mixed ? std::max(0.5 * need, 4e-6) : 0.9 * need;
+    }
+    if (all_done) break;
+    if ((rc = gmres_inner(h, k->z, nrhs, zn, eta, active, k->d, iters, est))) return rc;
+    // u += d for the active right-hand sides
+    {
+      std::vector<std::complex<double>> one((size_t)nrhs, 0.0);
+      for (int s = 0; s < nrhs; ++s) one[s] = active[s] ? 1.0 : 0.0;
+      const c128* tbl[1] = {k->d};
+      HSW_CUDA(cudaMemcpyAsync(k->dots, tbl, sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
+      HSW_CUDA(cudaMemcpyAsync(k->coef, one.data(), nrhs * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
+      axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->dots), 1,
+                                                           k->coef, 1, 1.0, u, N);
+      HSW_CUDA(cudaGetLastError());
+    }
+    if (!mixed) {
+      // FP64: the inner residual estimate is the FP64 one; stop when it met the tolerance
+      bool ok = true;
+      for (int s = 0; s < nrhs; ++s)
+        if (active[s] && !(est[s] * zn[s] <= tol * Mfn[s])) ok = false;
+      if (ok) { all_done = true; for (int s = 0; s < nrhs; ++s) done[s] = 1; }
+    }
+  }
+  // final FP64 residual
+  if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
+  sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
+  std::vector<double> rn;
+  if ((rc = norms(h, k->r, nrhs, rn))) return rc;
+  if (!all_done && mixed) {
+    if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
+    if ((rc = norms(h, k->z, nrhs, zn))) return rc;
+    all_done = true;
+    for (int s = 0; s < nrhs; ++s) if (!(zn[s] <= tol * Mfn[s])) all_done = false;
+  }
+  for (int s = 0; s < nrhs; ++s) {
+    if (iters_out) iters_out[s] = iters[s];
+    if (relres_out) relres_out[s] = fn[s] > 0 ? rn[s] / fn[s] : 0.0;
+  }
+  int st[2] = {0, -1};
+  HSW_CUDA(cudaMemcpy(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0] != 0) return st[0];
+  return all_done ? HSWEEP_OK : HSWEEP_ERR_NOT_CONVERGED;
+}
