@@ -1,0 +1,401 @@
+"""Benchmark: preconditioned Helmholtz solves per second on one GB300 (or N, weak scaling).
+
+Workload (default): n = 1023 (N = 1,046,529 unknowns), omega/2pi = 64, random smooth
+velocity c = 1 + 0.2 g (filter width 1/32, seed 1), PML 16 cells, 64 point sources at
+seeded positions, eps_H = 1e-6, mixed precision (complex64 H-factors and sweeps, FP64
+GMRES and refinement), all 64 right-hand sides in one batched solve.
+
+A step is one batched preconditioned solve of the 64 right-hand sides (GMRES on
+M A u = M f with the sweep apply of Algorithm 2.6 inside); the setup sweep
+(Algorithm 2.5) runs once before the timed region and is reported as setup_s.
+value = right-hand sides solved per second (to ||M(f - A u)|| <= tol ||M f||, which
+the parity tests tie to a relative error <= 1e-5 against the direct solve).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--fp64]
+
+Under torchrun every rank builds its own factorisation (a replica) and solves its
+own batch of 64 sources; there is no collective on the data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "n1023_random"
+METRIC = "preconditioned solves/sec at n=1023 (mixed vs FP64, rel err 1e-6); setup s"
+SOLVE_TOL = 1e-7
+
+
+def _tree_sizes(n, leaf=8):
+    L = 0
+    while -(-n // (1 << L)) > leaf:
+        L += 1
+    nn = 1 << (L + 1)
+    sz = [0] * nn
+    sz[1] = n
+    for v in range(1, nn // 2):
+        a = (sz[v] + 1) // 2
+        sz[2 * v], sz[2 * v + 1] = a, sz[v] - a
+    return L, sz
+
+
+def sweep_work(h, n, nrhs, elem_bytes):
+    """Algorithmic flops and HBM bytes of one sweep launch (Algorithm 2.6 over nrhs RHS).
+    Per layer step: leaves sz^2 complex MACs per RHS, every factor entry used twice
+    (reduction F^t x and expansion F q) per RHS; the factors are read once per step."""
+    L, sz = _tree_sizes(n)
+    leaf_e = sum(sz[v] * sz[v] for v in range(1 << L, 1 << (L + 1)))
+    lr = []
+    for m in range(n):
+        rk = h.layer_ranks(m)
+        lr.append(sum(sz[v] * rk[v] for v in range(2, 1 << (L + 1))))
+    steps = list(range(n)) + list(range(n - 1))      # forward layers, then backward layers
+    macs = sum(leaf_e + 2 * lr[m] for m in steps)
+    flops = 8.0 * nrhs * macs
+    fac_bytes = sum(leaf_e + lr[m] for m in steps) * elem_bytes
+    vec_bytes = nrhs * n * n * (16 + 16 + 2 * elem_bytes)   # read r, write z, w written + read
+    return flops, fac_bytes + vec_bytes, sum(lr) + n * leaf_e
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp32_alu_peak_tflops():
+    """FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the same workload.
+def cpu_sample(budget_s, applies_per_solve, n_layers_cap=None):
+    """Times the oracle's Algorithm 2.5 setup and Algorithm 2.6 apply on the first
+    layers of the workload until about budget_s of work, and scales the per-layer
+    apply time to the full sweep (2n - 1 layer steps).  Runs single-threaded."""
+    from oracle.assemble import Discretization
+    from oracle.hmatrix import Trunc, hinv, hsub, tree_depth
+    from oracle.sweep_h import tridiag_H
+    w = synth.workload(WORKLOAD)
+    disc = Discretization(w["c"], w["omega"], w["pml"])
+    n = disc.n
+    tr = Trunc(w["eps_H"], 48)
+    L = tree_depth(n, 8)
+    T = []
+    t0 = time.perf_counter()
+    m = 0
+    while m < n and (time.perf_counter() - t0 < 0.6 * budget_s or m < 3):
+        if n_layers_cap is not None and m >= n_layers_cap:
+            break
+        Amm = tridiag_H(disc.diag[m], disc.east[m, 1:-1], 0, 0, L)
+        S = Amm if m == 0 else hsub(Amm, T[m - 1].diagmul(dl=disc.A_off(m), dr=disc.A_off(m)), tr)
+        T.append(hinv(S, tr))
+        m += 1
+    t_setup = time.perf_counter() - t0
+    ms = len(T)
+    f = w["f"][0].reshape(n, n)
+    u = f[:ms].copy()
+    t1 = time.perf_counter()
+    wv = []
+    for k in range(ms):                       # forward steps on the sampled layers
+        wv.append(T[k].matvec(u[k]))
+        if k + 1 < ms:
+            u[k + 1] = u[k + 1] - disc.A_off(k + 1) * wv[k]
+    for k in range(ms - 2, -1, -1):           # backward steps
+        u[k] = wv[k] - T[k].matvec(disc.A_off(k + 1) * u[k + 1])
+    t_apply = time.perf_counter() - t1
+    per_step = t_apply / (2 * ms - 1)
+    t_solve = applies_per_solve * per_step * (2 * n - 1)
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle H-sweep (Algorithms 2.5/2.6, eps_H 1e-6) on the first %d of %d layers: "
+                      "setup %.1f s, %.1f ms per layer step; per-solve time = %.2f applies x %d layer steps"
+                      % (ms, n, t_setup, 1e3 * per_step, applies_per_solve, 2 * n - 1),
+            "setup_s_extrapolated": t_setup / ms * n, "seconds": t_setup + t_apply}
+
+
+def run_cpu_sample_subprocess(budget_s, applies_per_solve):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(budget_s),
+                          str(applies_per_solve)], capture_output=True, text=True, env=env, timeout=600)
+    for line in out.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
+
+
+# ---------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64", action="store_true", help="also time the FP64 sweep (nrhs = 1 per call)")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-sample", nargs=2, default=None)
+    args = ap.parse_args()
+
+    if args.cpu_sample is not None:
+        print(json.dumps(cpu_sample(float(args.cpu_sample[0]), float(args.cpu_sample[1]))))
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1007_4290_gb300 as hs
+
+    w = synth.workload(WORKLOAD)
+    n, omega, pml, eps = w["n"], w["omega"], w["pml"], w["eps_H"]
+    F = w["f"]
+    if rank > 0:   # every rank solves its own batch of sources
+        pts = synth.source_positions(n, F.shape[0], pml, 100 + rank)
+        F = np.stack([synth.source_delta(n, p) for p in pts])
+    nrhs = F.shape[0]
+    F = F.reshape(nrhs, n * n)
+    dev = torch.device("cuda", local)
+    c_d = torch.tensor(w["c"], device=dev)
+    f_d = torch.tensor(F, device=dev)
+    u_d = torch.zeros_like(f_d)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # setup (Algorithm 2.5), once
+    barrier()
+    t0 = time.perf_counter()
+    h = hs.hsweep_setup(c_d, omega, pml, eps, hs.default_opts(precision=hs.MIXED))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = h.info()
+
+    def step(u):
+        u.zero_()
+        _, it, rr = h.solve(f_d, SOLVE_TOL, u=u)
+        return it, rr
+
+    for _ in range(max(3, args.warmup)):
+        it, rr = step(u_d)
+    # L2: the 1 GB right-hand-side batch and the factors (GBs) exceed the 129 MB L2
+    h.stats(reset=True)
+    h.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            it, rr = step(u_d)
+        e1.record(stream)
+        barrier()
+    h.profile(False)
+    launches, sweeps, sweep_ms = h.stats(reset=True)
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = t.item()
+    total_solves = nrhs * args.steps * world
+    value = total_solves / (t_max / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    f_h = torch.tensor(F).pin_memory()
+    u_h = torch.empty_like(f_h).pin_memory()
+    for _ in range(2):
+        f_d.copy_(f_h, non_blocking=True)
+        step(u_d)
+        u_h.copy_(u_d, non_blocking=True)
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        f_d.copy_(f_h, non_blocking=True)
+        step(u_d)
+        u_h.copy_(u_d, non_blocking=True)
+    e3.record(stream)
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+    e2e_value = total_solves / (ms_e2e / 1e3)
+
+    # roofline of the dominant kernel (the sweep apply), from the live CUDA-event timing
+    flops, bytes_, stored = sweep_work(h, n, nrhs, info["bytes_per_entry"])
+    avg_s = (sweep_ms / max(1, sweeps)) / 1e3
+    peaks, src = _peaks()
+    alu_peak = fp32_alu_peak_tflops()
+    t_alu = flops / (alu_peak * 1e12)
+    t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (unit counts)"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "sweep_kernel<float,G,cluster>"
+    roof["launch_ms"] = avg_s * 1e3
+    roof["hbm_gbs_achieved"] = bytes_ / avg_s / 1e9
+    roof["hbm_frac"] = roof["hbm_gbs_achieved"] / peaks["hbm_gbs"]
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["algorithmic_bytes_per_launch"] = bytes_
+
+    fp64 = None
+    if args.fp64:
+        t0 = time.perf_counter()
+        h64 = hs.hsweep_setup(c_d, omega, pml, eps, hs.default_opts(precision=hs.FP64))
+        torch.cuda.synchronize()
+        s64 = time.perf_counter() - t0
+        u1 = torch.zeros_like(f_d[:1])
+        h64.solve(f_d[:1], SOLVE_TOL, u=u1)
+        k64 = 4
+        torch.cuda.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        its = []
+        for s in range(k64):
+            u1.zero_()
+            _, it1, _ = h64.solve(f_d[s:s + 1], SOLVE_TOL, u=u1)
+            its.append(it1[0])
+        e5.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"solves_per_s": k64 / (e4.elapsed_time(e5) / 1e3), "setup_s": s64, "nrhs_per_call": 1,
+                "gmres_iters": its}
+        h64.free()
+
+    cpu = None
+    if rank == 0 and world == 1:
+        applies = sweeps / max(1, args.steps)
+        try:
+            cpu = run_cpu_sample_subprocess(args.cpu_budget, applies)
+        except Exception as e:  # the baseline is reported, never required
+            cpu = {"error": str(e)[:200]}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors+sweeps / f64 Krylov",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "N": n * n, "omega_over_2pi": omega / (2 * np.pi),
+                       "pml": pml, "eps_H": eps, "nrhs": nrhs, "precision": "mixed", "tol": SOLVE_TOL,
+                       "parallelism": "replica per GPU, sources sharded" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (1 GB RHS batch, factors %.2f GB)" % (
+                           stored * info["bytes_per_entry"] / 1e9)},
+            "setup_s": setup_s,
+            "gmres_iters": {"min": min(it), "max": max(it), "mean": float(np.mean(it))},
+            "relres_max": max(rr),
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(f_h.numel() * 16),
+                    "d2h_bytes_per_step": int(u_h.numel() * 16)},
+            "gpu_launches": launches,
+            "sweep_launches_per_step": sweeps / args.steps,
+            "roofline": roof,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        if fp64 is not None:
+            line["fp64"] = fp64
+            line["mixed_over_fp64"] = value / fp64["solves_per_s"]
+        print(json.dumps(line))
+    h.free()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: each step is a bounded sample of the same workload on the host
+    cores (the oracle as it stands), on rank 0 only."""
+    if rank != 0:
+        return
+    vals = []
+    t0 = time.perf_counter()
+    budget = max(5.0, 20.0 / max(1, args.steps + args.warmup) * 3)
+    for k in range(args.warmup + args.steps):
+        r = run_cpu_sample_subprocess(budget, 4.0)
+        if k >= args.warmup:
+            vals.append(r)
+    elapsed = time.perf_counter() - t0
+    value = float(np.median([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "oracle complex128"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"] + " (4 applies per solve assumed)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": elapsed}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

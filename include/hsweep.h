@@ -177,6 +177,18 @@ HSWEEP_API int hsweep_export_layer(hsweep_t h, int m, hsw_c128* leaves, hsw_c128
 HSWEEP_API int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, const hsw_c128* factors,
                         const int* ranks);
 
+/*
+ * Instrumentation.  hsweep_profile(h, 1) brackets every sweep-kernel launch of the
+ * apply with a pair of CUDA events on the handle's stream (0 turns it off).
+ * hsweep_stats reports, since the last reset: the number of kernels this handle
+ * launched (launches), the number of timed sweep launches and their summed
+ * device time in milliseconds (sweep_ms).  Any output pointer may be NULL; reset != 0
+ * zeroes the counters afterwards.  hsweep_stats synchronises.
+ */
+HSWEEP_API int hsweep_profile(hsweep_t h, int enable);
+HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long long* sweep_launches,
+                            double* sweep_ms);
+
 /* Release every resource of the handle (NULL is allowed). */
 HSWEEP_API void hsweep_free(hsweep_t h);
 

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_
 
 EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_apply", "hsweep_matvec",
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
-            "hsweep_export_layer", "hsweep_import_layer", "hsweep_free"]
+            "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
+            "hsweep_stats"]
 
 
 class hsweep_opts(ctypes.Structure):
@@ -59,6 +60,8 @@ def load_library(path=LIB_PATH):
         "hsweep_export_layer": (I, [P, I, P, P, ctypes.POINTER(I)]),
         "hsweep_import_layer": (I, [P, I, P, P, ctypes.POINTER(I)]),
         "hsweep_free": (None, [P]),
+        "hsweep_profile": (I, [P, I]),
+        "hsweep_stats": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -131,6 +134,16 @@ class Handle:
         layer = ctypes.c_int(-1)
         code = _lib.hsweep_status(self.raw, ctypes.byref(layer))
         return code, layer.value
+
+    def profile(self, enable=True):
+        _check(_lib.hsweep_profile(self.raw, 1 if enable else 0), "hsweep_profile")
+
+    def stats(self, reset=False):
+        """(kernel launches, timed sweep launches, summed sweep device ms) since the last reset."""
+        a, b, ms = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+        _check(_lib.hsweep_stats(self.raw, 1 if reset else 0, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)),
+               "hsweep_stats")
+        return a.value, b.value, ms.value
 
     def layer_ranks(self, m):
         L = self.info()["L"]

@@ -56,6 +56,10 @@ static void destroy(hsweep_s* h) {
   if (!h) return;
   hsw_setup_free(h);
   hsw_krylov_free(h);
+  for (auto& pr : h->ev_sweep) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
+  h->ev_sweep.clear();
+  h->ev_free.clear();
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   delete h;
@@ -298,5 +302,32 @@ extern "C" int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, co
   HSW_CUDA(cudaMemcpy((char*)h->d_fac + (size_t)m * h->layer_stride * h->fac_elem(), buf.data(), buf.size(),
                       cudaMemcpyHostToDevice));
   HSW_CUDA(cudaMemcpy(h->d_rank + (size_t)m * h->nnodes, rk.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice));
+  return HSWEEP_OK;
+}
+
+extern "C" int hsweep_profile(hsweep_t h, int enable) {
+  if (!h) return HSWEEP_ERR_ARG;
+  h->prof = enable != 0;
+  return HSWEEP_OK;
+}
+
+extern "C" int hsweep_stats(hsweep_t h, int reset, long long* launches, long long* sweep_launches,
+                            double* sweep_ms) {
+  if (!h) return HSWEEP_ERR_ARG;
+  HSW_CUDA(cudaStreamSynchronize(h->stream));
+  double ms = 0;
+  for (auto& pr : h->ev_sweep) {
+    float t = 0;
+    HSW_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+    ms += t;
+  }
+  if (launches) *launches = h->nlaunch;
+  if (sweep_launches) *sweep_launches = (long long)h->ev_sweep.size();
+  if (sweep_ms) *sweep_ms = ms;
+  if (reset) {
+    h->nlaunch = 0;
+    for (auto& pr : h->ev_sweep) { h->ev_free.push_back(pr.first); h->ev_free.push_back(pr.second); }
+    h->ev_sweep.clear();
+  }
   return HSWEEP_OK;
 }

@@ -366,7 +366,20 @@ static int launch_sweep(hsweep_s* h, const SweepConfig& cfg, SweepArgs<R>& a, si
   }
   lc.attrs = at;
   lc.numAttrs = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->prof) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!h->ev_free.empty()) { *e = h->ev_free.back(); h->ev_free.pop_back(); }
+      else HSW_CUDA(cudaEventCreate(e));
+    }
+    HSW_CUDA(cudaEventRecord(e0, h->stream));
+  }
   HSW_CUDA(cudaLaunchKernelEx(&lc, kern, a));
+  h->nlaunch += 1;
+  if (h->prof) {
+    HSW_CUDA(cudaEventRecord(e1, h->stream));
+    h->ev_sweep.push_back({e0, e1});
+  }
   return HSWEEP_OK;
 }
 

@@ -74,6 +74,7 @@ int hsw_assemble(hsweep_s* h, double pml_C, int pml_form) {
   dim3 grid(div_up(h->n, 128), h->n);
   assemble_kernel<<<grid, 128, 0, h->stream>>>(h->n, h->h, eta, pref, h->omega, h->d_c,
                                                 h->d_diag, h->d_east, h->d_north, h->d_s1s2);
+  h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   return HSWEEP_OK;
 }
@@ -83,6 +84,7 @@ int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs) {
   dim3 grid(div_up(h->n, 128), h->n, nrhs < 8 ? nrhs : 8);
   matvec_kernel<<<grid, 128, 0, h->stream>>>(h->n, (long long)h->N, nrhs, h->d_diag, h->d_east,
                                               h->d_north, x, y);
+  h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   return HSWEEP_OK;
 }

@@ -1,5 +1,6 @@
 // Internal state of an hsweep handle, shared by the translation units of the library.
 #pragma once
+#include <utility>
 #include <vector>
 #include "common.cuh"
 
@@ -68,6 +69,13 @@ struct hsweep_s {
   KrylovWork* kw = nullptr;
 
   std::vector<void*> allocs;   // every device allocation owned by the handle
+
+  // instrumentation: kernel launches made by this handle, and (when prof is set) a
+  // pair of CUDA events around every sweep-kernel launch on the handle's stream
+  long long nlaunch = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sweep;
 
   size_t fac_elem() const { return prec == HSWEEP_FP64 ? sizeof(c128) : sizeof(c64); }
 };

@@ -151,7 +151,9 @@ static int basis(hsweep_s* h, int i, c128** out) {
 static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs, std::vector<std::complex<double>>& hd) {
   KrylovWork* k = h->kw;
   dots_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(k->d_V + first, nv, w, h->N, k->partial);
+  h->nlaunch += 1;
   reduce_partials<<<nrhs * nv, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
+  h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   hd.resize((size_t)nrhs * nv);
   HSW_CUDA(cudaMemcpyAsync(hd.data(), k->dots, (size_t)nrhs * nv * sizeof(c128), cudaMemcpyDeviceToHost, h->stream));
@@ -162,16 +164,14 @@ static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs,
 // ||x[s]|| for every s, on the host
 static int norms(hsweep_s* h, const c128* x, int nrhs, std::vector<double>& out) {
   KrylovWork* k = h->kw;
-  // use the pointer table slot after the basis for x
   const c128* tbl[1] = {x};
-  c128** d_tmp = k->d_V + (k->vmax - 1);
-  (void)d_tmp;
-  static_assert(sizeof(c128*) == 8, "pointer size");
   // a one-entry table lives in the coef buffer (it is not in use while norms run)
   HSW_CUDA(cudaMemcpyAsync(k->coef, tbl, sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
   dots_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->coef), 1, x,
                                                                h->N, k->partial);
+  h->nlaunch += 1;
   reduce_partials<<<nrhs, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
+  h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   std::vector<std::complex<double>> hd(nrhs);
   HSW_CUDA(cudaMemcpyAsync(hd.data(), k->dots, nrhs * sizeof(c128), cudaMemcpyDeviceToHost, h->stream));
@@ -213,6 +213,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     std::vector<double> zn(znrm);
     HSW_CUDA(cudaMemcpyAsync(k->nrm, zn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     scale_kernel<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
+    h->nlaunch += 1;
   }
   std::vector<cd> hd, hd2;
   int j = 0;
@@ -233,11 +234,13 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
       for (size_t e = 0; e < hd.size(); ++e) hcol[e] += hd[e];
       HSW_CUDA(cudaMemcpyAsync(k->coef, hd.data(), hd.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
       axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
+      h->nlaunch += 1;
     }
     std::vector<double> wn;
     if ((rc = norms(h, k->w, nrhs, wn))) return rc;
     HSW_CUDA(cudaMemcpyAsync(k->nrm, wn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     scale_kernel<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
+    h->nlaunch += 1;
     for (int s = 0; s < nrhs; ++s) {
       if (!run[s]) continue;
       cd* Hs = H[s].data();
@@ -283,6 +286,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
       for (int i = 0; i < kmax; ++i) Yc[(size_t)s * kmax + i] = Y[(size_t)s * maxit + i];
     HSW_CUDA(cudaMemcpyAsync(k->coef, Yc.data(), Yc.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
     axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
+    h->nlaunch += 1;
     HSW_CUDA(cudaGetLastError());
   }
   HSW_CUDA(cudaStreamSynchronize(h->stream));
@@ -308,6 +312,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
     // r = f - A u, z = M r
     if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
     sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
+    h->nlaunch += 1;
     if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
     if ((rc = norms(h, k->z, nrhs, zn))) return rc;
     std::vector<char> active(nrhs, 0);
@@ -332,6 +337,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       HSW_CUDA(cudaMemcpyAsync(k->coef, one.data(), nrhs * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
       axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->dots), 1,
                                                            k->coef, 1, 1.0, u, N);
+      h->nlaunch += 1;
       HSW_CUDA(cudaGetLastError());
     }
     if (!mixed) {
@@ -345,6 +351,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
   // final FP64 residual
   if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
   sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
+  h->nlaunch += 1;
   std::vector<double> rn;
   if ((rc = norms(h, k->r, nrhs, rn))) return rc;
   if (!all_done && mixed) {

@@ -802,31 +802,46 @@ static int factor_impl(hsweep_s* h) {
     const Cx<R>* Tprev = m > 0 ? fac + (long long)(m - 1) * h->layer_stride : nullptr;
     const int* rprev = m > 0 ? h->d_rank + (long long)(m - 1) * nn : nullptr;
     schur_leaves<R><<<h->nleaves, 64, 0, st>>>(g, m, h->d_diag, h->d_east, h->d_north, Tprev, S_leaf);
-    if (nn > 2)
+    h->nlaunch += 1;
+    if (nn > 2) {
       schur_factors<R><<<nn - 2, kBlk, 0, st>>>(g, m, h->d_east, h->d_north, Tprev, h->d_off, rprev, S_F,
                                                  w->S_rank);
+      h->nlaunch += 1;
+    }
     HSW_CUDA(cudaMemsetAsync(w->G_rank, 0, nn * sizeof(int), st));
     leaf_inverse<R><<<h->nleaves, 128, 0, st>>>(g, m, S_leaf, G_leaf, h->d_status);
+    h->nlaunch += 1;
     for (int d = L - 1; d >= 0; --d) {
       const int n_below2 = (d + 2 <= L) ? (1 << (L + 1)) - (1 << (d + 2)) : 0;
       const int n_below1 = (1 << (L + 1)) - (1 << (d + 1));
       const int ntau_d = 1 << d;
-      if (n_below2 > 0)
+      if (n_below2 > 0) {
         tsmm_reduce<R><<<n_below2, kBlk, 0, st>>>(g, d, G_F, w->G_rank, S_F, w->S_rank, Qr);
+        h->nlaunch += 1;
+      }
       tsmm_expand<R><<<dim3(div_up(h->n, 128), KCAP), 128, 0, st>>>(g, d, G_leaf, G_F, w->G_rank, S_F,
                                                                      w->S_rank, Qr, Y);
+      h->nlaunch += 1;
       core_dots<R><<<dim3(2 * ntau_d, 8), kBlk, 0, st>>>(g, d, S_F, w->S_rank, Y, PQ);
+      h->nlaunch += 1;
       core_inverse<R><<<ntau_d, 512, core_smem, st>>>(g, d, m, w->S_rank, PQ, M, h->d_status);
+      h->nlaunch += 1;
       woodbury_form<R><<<dim3(div_up(h->n, 128), KCAP), 128, 0, st>>>(g, d, w->S_rank, Y, M, Wv, G_F, w->G_rank);
+      h->nlaunch += 1;
       woodbury_append<R><<<n_below1, kBlk, 0, st>>>(g, d, w->S_rank, Y, Wv, G_F, w->G_rank, G_leaf);
+      h->nlaunch += 1;
       qr_cgs2<R><<<n_below1, kBlk, qr_smem, st>>>(g, d, G_F, w->G_rank, Rb, w->qcols);
+      h->nlaunch += 1;
       svd_jacobi<R><<<n_below1 / 2, kBlk, svd_smem, st>>>(g, d, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx,
                                                          w->newrank);
+      h->nlaunch += 1;
       recompress_apply<R><<<n_below1, kBlk, 0, st>>>(g, d, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);
+      h->nlaunch += 1;
       std::swap(G_F, G_F2);
     }
     store_layer<R><<<nn, kBlk, 0, st>>>(g, G_leaf, G_F, w->G_rank, fac + (long long)m * h->layer_stride,
                                         h->d_off, h->d_rank + (long long)m * nn);
+    h->nlaunch += 1;
     HSW_CUDA(cudaGetLastError());
   }
   w->G_F = G_F;
