@@ -189,6 +189,29 @@ HSWEEP_API int hsweep_profile(hsweep_t h, int enable);
 HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long long* sweep_launches,
                             double* sweep_ms);
 
+/*
+ * z = M r exactly as hsweep_apply, for callers that must not allocate device memory
+ * during the call: code running where cudaMalloc is forbidden or unsafe, such as a
+ * framework that owns and accounts for all device memory, a latency-critical loop in
+ * which cudaMalloc's implicit device synchronisation is not acceptable, or a memory
+ * budget that is already fully committed.  (The paper has no counterpart: this is a
+ * property of the library, not of the method.)
+ *   - Scratch comes from one fixed device array inside the library, of
+ *     HSWEEP_NOALLOC_SCRATCH_BYTES bytes (32 MiB), which every GPU that loads the
+ *     library reserves until the process exits.  A call whose scratch need
+ *     (about nrhs * n*n * 8 bytes in HSWEEP_MIXED, * 16 in HSWEEP_FP64, plus a few MiB)
+ *     exceeds it returns HSWEEP_ERR_ARG and does nothing.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with the handle's device current); make that first call before any
+ *     stream capture.  The current device must be the handle's device.
+ *   - Every call shares the one array and it keeps the last call's contents; calls
+ *     whose GPU work overlaps (other streams, other handles, other threads) race on it.
+ *   - r and z are as in hsweep_apply.  No cudaMalloc, cudaFree or allocating library
+ *     routine is called.  Stream-ordered; returns after enqueue.
+ */
+#define HSWEEP_NOALLOC_SCRATCH_BYTES (32u << 20)
+HSWEEP_API int hsweep_apply_noalloc(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs);
+
 /* Release every resource of the handle (NULL is allowed). */
 HSWEEP_API void hsweep_free(hsweep_t h);
 

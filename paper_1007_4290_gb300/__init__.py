@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_
 EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_apply", "hsweep_matvec",
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
-            "hsweep_stats"]
+            "hsweep_stats", "hsweep_apply_noalloc"]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class hsweep_opts(ctypes.Structure):
@@ -62,6 +63,7 @@ def load_library(path=LIB_PATH):
         "hsweep_free": (None, [P]),
         "hsweep_profile": (I, [P, I]),
         "hsweep_stats": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]),
+        "hsweep_apply_noalloc": (I, [P, P, P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +249,15 @@ def hsweep_create(c, omega, pml_width, eps_H, opts=None):
 
 def hsweep_apply(h, r, z=None):
     return h.apply(r, z)
+
+
+def hsweep_apply_noalloc(h, r, z):
+    """z = M r with the library's fixed scratch array (no device allocation); r and z
+    are preallocated (nrhs, n*n) complex128 CUDA tensors."""
+    r2 = r.reshape(-1, h.N)
+    _check(_lib.hsweep_apply_noalloc(h.raw, _ptr(r2, torch.complex128), _ptr(z, torch.complex128), r2.shape[0]),
+           "hsweep_apply_noalloc")
+    return z
 
 
 def hsweep_matvec(h, x, y=None):

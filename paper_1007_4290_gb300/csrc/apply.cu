@@ -446,3 +446,65 @@ int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs) {
   if (h->prec == HSWEEP_FP64) return apply_impl<double>(h, r, z, nrhs, cfg);
   return apply_impl<float>(h, r, z, nrhs, cfg);
 }
+
+// ---------------------------------------------------------------------------------------
+// The same sweep with caller-provided scratch (the w cache and the team exchange slots
+// carved out of one buffer).  Nothing is allocated here.
+
+static long long align_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs) {
+  if (nrhs <= 0) return 0;
+  SweepConfig cfg = choose_config(h, nrhs);
+  const long long es = h->prec == HSWEEP_FP64 ? (long long)sizeof(c128) : (long long)sizeof(c64);
+  const long long w = (long long)nrhs * h->N * es;
+  const long long x = 2LL * cfg.nteams * (cfg.dC > 0 ? cfg.dC : 1) * cfg.C * h->r_max * cfg.G * es;
+  return (size_t)(align_up(w, 256) + align_up(x, 256));
+}
+
+template <typename R>
+static int apply_scratch_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, const SweepConfig& cfg,
+                              unsigned char* scratch) {
+  const size_t es = sizeof(Cx<R>);
+  SweepArgs<R> a;
+  a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.r_max = h->r_max; a.nnodes = h->nnodes;
+  a.dC = cfg.dC; a.C = cfg.C; a.nteams = cfg.nteams; a.nrhs = nrhs;
+  a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
+  a.slab_max = h->tree.maxsz(cfg.dC);
+  a.N = h->N; a.layer_stride = h->layer_stride;
+  a.lo = h->d_lo; a.sz = h->d_sz; a.off = h->d_off;
+  a.fac = reinterpret_cast<const Cx<R>*>(h->d_fac);
+  a.rank = h->d_rank; a.north = h->d_north;
+  a.r = r; a.z = z;
+  a.w = reinterpret_cast<Cx<R>*>(scratch);
+  a.xch = reinterpret_cast<Cx<R>*>(scratch + align_up((long long)nrhs * h->N * (long long)es, 256));
+  a.status = h->d_status; a.bar = h->d_bar;
+  size_t hdr = (size_t)(2 * h->nnodes + 32 + a.slab_max) * sizeof(int);
+  hdr = (hdr + 15) & ~size_t(15);
+  long long qloc = 0;
+  for (int d = cfg.dC + 1; d <= h->L; ++d) {
+    int mx = h->tree.maxsz(d);
+    qloc += (long long)(1 << (d - cfg.dC)) * (mx < h->r_max ? mx : h->r_max) * cfg.G;
+  }
+  size_t smem = hdr + es * (size_t)(2LL * cfg.G * a.slab_max + (long long)(cfg.dC > 0 ? cfg.dC : 1) * h->r_max * cfg.G + qloc);
+  if (smem > 227 * 1024) return HSWEEP_ERR_ARG;
+  const bool prof = h->prof;
+  h->prof = false;   // no events are created on this path
+  int rc;
+  if (cfg.grid) {
+    if (cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess) { h->prof = prof; return HSWEEP_ERR_CUDA; }
+    rc = dispatch_G<R, true>(h, cfg, a, smem);
+  } else {
+    rc = dispatch_G<R, false>(h, cfg, a, smem);
+  }
+  h->prof = prof;
+  return rc;
+}
+
+int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scratch, size_t bytes) {
+  if (nrhs <= 0) return HSWEEP_OK;
+  if (hsw_apply_scratch_bytes(h, nrhs) > bytes) return HSWEEP_ERR_ARG;
+  SweepConfig cfg = choose_config(h, nrhs);
+  if (h->prec == HSWEEP_FP64) return apply_scratch_impl<double>(h, r, z, nrhs, cfg, (unsigned char*)scratch);
+  return apply_scratch_impl<float>(h, r, z, nrhs, cfg, (unsigned char*)scratch);
+}

@@ -89,6 +89,8 @@ int hsw_assemble(hsweep_s* h, double pml_C, int pml_form);
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
 // apply.cu
 int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs);
+size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs);
+int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scratch, size_t bytes);
 // setup.cu
 int hsw_factor(hsweep_s* h);
 void hsw_setup_free(hsweep_s* h);

@@ -1,0 +1,56 @@
+// hsweep_apply_noalloc: the sweep apply for callers that cannot allocate device memory.
+//
+// Its scratch (the cache of T~_m u_m between the two sweeps and the exchange slots of
+// the sweep teams) lives in the fixed device array below instead of buffers allocated
+// on demand.  The array is defined at file scope, so every GPU that loads this library
+// reserves it until the process exits.
+#include <mutex>
+#include "handle.h"
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = HSWEEP_NOALLOC_SCRATCH_BYTES;   // 32 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (in host code the array's name is only a host-side stand-in).
+int scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return HSWEEP_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HSWEEP_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return HSWEEP_OK;
+}
+
+}  // namespace
+
+extern "C" int hsweep_apply_noalloc(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs) {
+  if (!h || nrhs < 0 || (nrhs > 0 && (!r || !z))) return HSWEEP_ERR_ARG;
+  if (nrhs == 0) return HSWEEP_OK;
+  const char* rb = (const char*)r;
+  const char* zb = (const char*)z;
+  size_t bytes = (size_t)nrhs * h->N * sizeof(hsw_c128);
+  if (rb < zb + bytes && zb < rb + bytes) return HSWEEP_ERR_ARG;
+  if (hsw_apply_scratch_bytes(h, nrhs) > kNoAllocScratchBytes) return HSWEEP_ERR_ARG;   // too large
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return HSWEEP_ERR_CUDA; }
+  if (dev != h->device) return HSWEEP_ERR_ARG;
+  void* scratch = nullptr;
+  int rc = scratch_address(dev, &scratch);
+  if (rc != HSWEEP_OK) return rc;
+  return hsw_apply_scratch(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs, scratch,
+                           kNoAllocScratchBytes);
+}
