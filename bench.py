@@ -303,7 +303,9 @@ def main():
                 "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel"] = "sweep_kernel<float,G,cluster>"
+    plan = h.sweep_plan(nrhs)
+    roof["kernel"] = ("sweep_tma_kernel" if plan["tma"] else "sweep_kernel") + "<c64>"
+    roof["plan"] = plan
     roof["launch_ms"] = avg_s * 1e3
     roof["hbm_gbs_achieved"] = bytes_ / avg_s / 1e9
     roof["hbm_frac"] = roof["hbm_gbs_achieved"] / peaks["hbm_gbs"]

@@ -71,6 +71,8 @@ typedef struct {
   int refine_max;    /* outer FP64 refinement steps in HSWEEP_MIXED (default 8) */
   int team;          /* CTAs per sweep team (power of two, 0 = automatic) */
   int groups;        /* right-hand sides per sweep team (1, 2, 4 or 8; 0 = automatic) */
+  int sweep_kernel;  /* 0: TMA-staged sweep when its shared-memory plan fits (default);
+                        1: the basic sweep that reads the factors from global memory */
 } hsweep_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -188,6 +190,15 @@ HSWEEP_API int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, co
 HSWEEP_API int hsweep_profile(hsweep_t h, int enable);
 HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long long* sweep_launches,
                             double* sweep_ms);
+
+/*
+ * The launch plan the apply would use for nrhs right-hand sides (diagnostics):
+ * out[0] 1 if the TMA-staged sweep kernel is used (0: the basic kernel), out[1] CTAs per
+ * team, out[2] right-hand sides per team, out[3] teams, out[4] 1 for a whole-grid team,
+ * out[5] dynamic shared memory per CTA in bytes, out[6] largest per-step factor record
+ * of one CTA in bytes, out[7] leaves per reduction chunk.
+ */
+HSWEEP_API int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8);
 
 /*
  * z = M r exactly as hsweep_apply, for callers that must not allocate device memory

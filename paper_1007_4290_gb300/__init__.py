@@ -25,14 +25,15 @@ STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_
 EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_apply", "hsweep_matvec",
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
-            "hsweep_stats", "hsweep_apply_noalloc"]
+            "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class hsweep_opts(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("r_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("pml_C", ctypes.c_double), ("pml_form", ctypes.c_int), ("gmres_max_it", ctypes.c_int),
-                ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int)]
+                ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int),
+                ("sweep_kernel", ctypes.c_int)]
 
 
 class HSweepError(RuntimeError):
@@ -64,6 +65,7 @@ def load_library(path=LIB_PATH):
         "hsweep_profile": (I, [P, I]),
         "hsweep_stats": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]),
         "hsweep_apply_noalloc": (I, [P, P, P, I]),
+        "hsweep_sweep_plan": (I, [P, I, ctypes.POINTER(LL)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -146,6 +148,12 @@ class Handle:
         _check(_lib.hsweep_stats(self.raw, 1 if reset else 0, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)),
                "hsweep_stats")
         return a.value, b.value, ms.value
+
+    def sweep_plan(self, nrhs):
+        out = (ctypes.c_longlong * 8)()
+        _check(_lib.hsweep_sweep_plan(self.raw, nrhs, out), "hsweep_sweep_plan")
+        keys = ["tma", "team_ctas", "rhs_per_team", "teams", "grid", "smem", "record_bytes_max", "leaves_per_chunk"]
+        return dict(zip(keys, list(out)))
 
     def layer_ranks(self, m):
         L = self.info()["L"]

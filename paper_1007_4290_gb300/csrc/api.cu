@@ -49,6 +49,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->refine_max = 8;
   o->team = 0;
   o->groups = 0;
+  o->sweep_kernel = 0;
   return HSWEEP_OK;
 }
 
@@ -82,7 +83,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       !(eps_H >= 0) || opt.leaf < 2 || opt.leaf > 8 || opt.r_max < 1 || opt.r_max > 56 ||
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
-      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0)
+      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 1)
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -117,6 +118,12 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   }
   o = (o + 31) & ~31LL;   // keep every layer 256-byte aligned
   h->layer_stride = o;
+  // packed copy: worst-case record of every leaf (all ranks at r_max), layers 256-byte aligned
+  {
+    const long long rs = h->r_max | 1;
+    const long long rec = (long long)h->leaf * h->leaf + (long long)h->L * h->leaf * rs + 1;
+    h->pack_stride = ((long long)h->nleaves * rec + 31) & ~31LL;
+  }
 
   const size_t N = (size_t)h->N;
   TRY(hsw_alloc(h, (void**)&h->d_lo, h->nnodes * sizeof(int)));
@@ -129,6 +136,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   TRY(hsw_alloc(h, (void**)&h->d_east, (size_t)n * (n + 1) * sizeof(c128)));
   TRY(hsw_alloc(h, (void**)&h->d_north, (size_t)(n + 1) * n * sizeof(c128)));
   TRY(hsw_alloc(h, (void**)&h->d_s1s2, N * sizeof(c128)));
+  TRY(hsw_alloc(h, &h->d_pack, (size_t)n * h->pack_stride * h->fac_elem()));
+  TRY(hsw_alloc(h, (void**)&h->d_recoff, (size_t)n * (h->nleaves + 1) * sizeof(long long)));
   TRY(hsw_alloc(h, (void**)&h->d_status, 2 * sizeof(int)));
   TRY(hsw_alloc(h, (void**)&h->d_bar, 2 * sizeof(unsigned)));
   TRYC(cudaMemcpyAsync(h->d_lo, h->tree.lo.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -136,6 +145,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   TRYC(cudaMemcpyAsync(h->d_off, h->off.data(), h->nnodes * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   TRYC(cudaMemsetAsync(h->d_fac, 0, (size_t)n * h->layer_stride * h->fac_elem(), h->stream));
   TRYC(cudaMemsetAsync(h->d_rank, 0, (size_t)n * h->nnodes * sizeof(int), h->stream));
+  TRYC(cudaMemsetAsync(h->d_recoff, 0, (size_t)n * (h->nleaves + 1) * sizeof(long long), h->stream));
   TRYC(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), h->stream));
   TRYC(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
   TRYC(cudaMemcpyAsync(h->d_c, c_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -171,6 +181,7 @@ extern "C" int hsweep_setup(const double* c_dev, double omega, int n, int pml_wi
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = HSWEEP_ERR_CUDA;
   }
   hsw_setup_free(h);   // the setup workspace is not needed once the factors are stored
+  if (rc == HSWEEP_OK) rc = hsw_pack(h, 0, h->n);
   if (rc == HSWEEP_OK) {
     int st[2] = {0, -1};
     if (cudaMemcpy(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HSWEEP_ERR_CUDA;
@@ -302,7 +313,7 @@ extern "C" int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, co
   HSW_CUDA(cudaMemcpy((char*)h->d_fac + (size_t)m * h->layer_stride * h->fac_elem(), buf.data(), buf.size(),
                       cudaMemcpyHostToDevice));
   HSW_CUDA(cudaMemcpy(h->d_rank + (size_t)m * h->nnodes, rk.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice));
-  return HSWEEP_OK;
+  return hsw_pack(h, m, m + 1);
 }
 
 extern "C" int hsweep_profile(hsweep_t h, int enable) {
@@ -330,4 +341,9 @@ extern "C" int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
     h->ev_sweep.clear();
   }
   return HSWEEP_OK;
+}
+
+extern "C" int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8) {
+  if (!h || !out8 || nrhs < 1) return HSWEEP_ERR_ARG;
+  return hsw_tma_plan(h, nrhs, out8);
 }

@@ -57,6 +57,16 @@ struct hsweep_s {
   c128* d_north = nullptr;
   c128* d_s1s2 = nullptr;
 
+  // Leaf-major packed copy of the factors, read by the sweep: for every layer and leaf
+  // one contiguous record [leaf block | rows of the leaf in F_v for depths 1..L], so the
+  // rows of any subtree form one contiguous byte range (see pack.cu).
+  void* d_pack = nullptr;
+  long long pack_stride = 0;             // entries per layer (worst-case capacity)
+  long long* d_recoff = nullptr;         // [n][nleaves + 1] record offsets within a layer
+  std::vector<long long> slab_bytes_max; // per slab depth dC: largest slab record in bytes
+  int rank_max = 0;
+  bool pack_valid = false;
+
   int* d_status = nullptr;     // [2]
   unsigned* d_bar = nullptr;   // grid barrier words [2]
 
@@ -91,6 +101,13 @@ int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
 int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs);
 size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs);
 int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scratch, size_t bytes);
+// pack.cu
+int hsw_pack(hsweep_s* h, int m0, int m1);
+// sweep_tma.cu
+int hsw_apply_tma(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch = nullptr,
+                  size_t scratch_bytes = 0);
+size_t hsw_apply_tma_scratch_bytes(hsweep_s* h, int nrhs);
+int hsw_tma_plan(hsweep_s* h, int nrhs, long long* out8);
 // setup.cu
 int hsw_factor(hsweep_s* h);
 void hsw_setup_free(hsweep_s* h);
