@@ -188,6 +188,11 @@ def main():
     ap.add_argument("--fp64", action="store_true", help="also time the FP64 sweep (nrhs = 1 per call)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--cpu-sample", nargs=2, default=None)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synthetic workload (n1023_random, n511_lens, n64_const, n2047_random)")
+    ap.add_argument("--apply-only", type=int, default=0, metavar="NRHS",
+                    help="time only the sweep apply (Algorithm 2.6) on NRHS right-hand sides")
+    ap.add_argument("--setup-only", action="store_true", help="time only the setup sweep (Algorithm 2.5)")
     args = ap.parse_args()
 
     if args.cpu_sample is not None:
@@ -201,6 +206,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
+    if args.apply_only or args.setup_only:
+        run_parts(args)
+        return
 
     import torch
     import torch.distributed as dist
@@ -209,7 +217,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1007_4290_gb300 as hs
 
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     n, omega, pml, eps = w["n"], w["omega"], w["pml"], w["eps_H"]
     F = w["f"]
     if rank > 0:   # every rank solves its own batch of sources
@@ -372,6 +380,44 @@ def main():
     h.free()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_parts(args):
+    """Component timings on one GPU: the setup sweep alone, or the apply alone."""
+    import torch
+    import paper_1007_4290_gb300 as hs
+    w = synth.workload(args.workload)
+    n = w["n"]
+    c_d = torch.tensor(w["c"], device="cuda")
+    prec = hs.FP64 if args.fp64 else hs.MIXED
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = hs.hsweep_setup(c_d, w["omega"], w["pml"], w["eps_H"], hs.default_opts(precision=prec))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = {"workload": args.workload, "n": n, "precision": "fp64" if args.fp64 else "mixed", "setup_s": setup_s,
+           "info": h.info()}
+    if args.apply_only:
+        nrhs = args.apply_only
+        F = w["f"].reshape(w["f"].shape[0], -1)
+        reps = (nrhs + F.shape[0] - 1) // F.shape[0]
+        R = torch.tensor(np.concatenate([F] * reps)[:nrhs], device="cuda")
+        Z = torch.empty_like(R)
+        for _ in range(max(1, args.warmup)):
+            h.apply(R, Z)
+        h.profile(True)
+        h.stats(reset=True)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            h.apply(R, Z)
+        torch.cuda.synchronize()
+        launches, sweeps, sweep_ms = h.stats(reset=True)
+        flops, bytes_, _ = sweep_work(h, n, nrhs, out["info"]["bytes_per_entry"])
+        avg = sweep_ms / max(1, sweeps)
+        out.update({"nrhs": nrhs, "apply_ms": avg, "plan": h.sweep_plan(nrhs),
+                    "tflops": flops / (avg / 1e3) / 1e12, "hbm_gbs": bytes_ / (avg / 1e3) / 1e9})
+    h.free()
+    print(json.dumps(out))
 
 
 def run_reference(args, world, rank):

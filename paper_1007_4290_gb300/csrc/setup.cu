@@ -793,6 +793,17 @@ static int factor_impl(hsweep_s* h) {
   const size_t core_smem = (size_t)(2 * KCAP) * (2 * KCAP) * es + 32 * sizeof(R) + (2 * KCAP + 1) * sizeof(int) + 16;
   const size_t qr_smem = (size_t)(h->tree.maxsz(1) + WCAP) * es + 32 * sizeof(R) + 16;
   const size_t svd_smem = (size_t)WCAP * WCAP * es + (WCAP + 1) * (sizeof(R) + sizeof(int)) + 64;
+  // one shared-memory carveout for every kernel of the layer loop, so that consecutive
+  // launches do not reconfigure the SMs' L1/shared split
+  {
+    const void* ks[] = {(const void*)schur_leaves<R>, (const void*)schur_factors<R>, (const void*)leaf_inverse<R>,
+                        (const void*)tsmm_reduce<R>, (const void*)tsmm_expand<R>, (const void*)core_dots<R>,
+                        (const void*)core_inverse<R>, (const void*)woodbury_form<R>, (const void*)woodbury_append<R>,
+                        (const void*)qr_cgs2<R>, (const void*)svd_jacobi<R>, (const void*)recompress_apply<R>,
+                        (const void*)store_layer<R>};
+    for (const void* k : ks)
+      HSW_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+  }
   HSW_CUDA(cudaFuncSetAttribute(core_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem));
   HSW_CUDA(cudaFuncSetAttribute(qr_cgs2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem));
   HSW_CUDA(cudaFuncSetAttribute(svd_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)svd_smem));
@@ -824,15 +835,15 @@ static int factor_impl(hsweep_s* h) {
       h->nlaunch += 1;
       core_dots<R><<<dim3(2 * ntau_d, 8), kBlk, 0, st>>>(g, d, S_F, w->S_rank, Y, PQ);
       h->nlaunch += 1;
-      core_inverse<R><<<ntau_d, 512, core_smem, st>>>(g, d, m, w->S_rank, PQ, M, h->d_status);
+      core_inverse<R><<<ntau_d, 1024, core_smem, st>>>(g, d, m, w->S_rank, PQ, M, h->d_status);
       h->nlaunch += 1;
       woodbury_form<R><<<dim3(div_up(h->n, 128), KCAP), 128, 0, st>>>(g, d, w->S_rank, Y, M, Wv, G_F, w->G_rank);
       h->nlaunch += 1;
       woodbury_append<R><<<n_below1, kBlk, 0, st>>>(g, d, w->S_rank, Y, Wv, G_F, w->G_rank, G_leaf);
       h->nlaunch += 1;
-      qr_cgs2<R><<<n_below1, kBlk, qr_smem, st>>>(g, d, G_F, w->G_rank, Rb, w->qcols);
+      qr_cgs2<R><<<n_below1, 1024, qr_smem, st>>>(g, d, G_F, w->G_rank, Rb, w->qcols);
       h->nlaunch += 1;
-      svd_jacobi<R><<<n_below1 / 2, kBlk, svd_smem, st>>>(g, d, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx,
+      svd_jacobi<R><<<n_below1 / 2, 1024, svd_smem, st>>>(g, d, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx,
                                                          w->newrank);
       h->nlaunch += 1;
       recompress_apply<R><<<n_below1, kBlk, 0, st>>>(g, d, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);

@@ -89,8 +89,8 @@ struct TmaArgs {
   int* status;
   unsigned* bar;
   // shared-memory plan (byte offsets)
-  unsigned o_stage[2], o_rowoff[2], o_trk[3], o_ro[3], o_vin[2], o_vn[2], o_lo, o_sz, o_leafnode, o_dtab, o_x[2],
-      o_qanc, o_qloc, o_ypart, o_mbar, o_flags;
+  unsigned o_stage[2], o_rowoff[2], o_trk[3], o_ro[3], o_vin[2], o_vn[2], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_boff, o_x[2],
+      o_qanc, o_qloc, o_mbar, o_flags;
 };
 
 // Bounded-spin barrier over the whole cooperative grid (see apply.cu).
@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
   int* s_flags = reinterpret_cast<int*>(sm + a.o_flags);    // [0]: this CTA failed
   Cx<R>* qanc = reinterpret_cast<Cx<R>*>(sm + a.o_qanc);
   Cx<R>* qloc = reinterpret_cast<Cx<R>*>(sm + a.o_qloc);
-  Cx<R>* ypart = reinterpret_cast<Cx<R>*>(sm + a.o_ypart);
 
   for (int v = tid; v < a.nnodes; v += blockDim.x) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
   __syncthreads();
@@ -163,7 +162,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
       const int nodes = d <= dC ? 1 : (1 << (d - dC));
       const int qcap = d <= dC ? a.rcap : min(rows, a.rcap);
       int kw = 1;
-      while (kw < qcap && kw < 16) kw <<= 1;
+      const int kwmax = d <= dC ? 8 : 16;
+      while (kw < qcap && kw < kwmax) kw <<= 1;
       dt[DT_KW + d] = kw;
       dt[DT_NODES + d] = nodes;
       dt[DT_QCAP + d] = qcap;
@@ -171,6 +171,18 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
       wsum += nodes * ((qcap + kw - 1) / kw) * GQ;
       dt[DT_QBASE + d] = qb;
       if (d > dC) qb += nodes * qcap * G;
+    }
+    // descriptors of every reduction warp-item: d | kc << 4 | jn << 12 | gq << 24
+    {
+      int* wdesc = reinterpret_cast<int*>(sm + a.o_wdesc);
+      int wi = 0;
+      for (int d = 1; d <= L; ++d) {
+        const int nodes = dt[DT_NODES + d], qcap = dt[DT_QCAP + d], kw = dt[DT_KW + d];
+        const int nkc = (qcap + kw - 1) / kw;
+        for (int gq = 0; gq < GQ; ++gq)
+          for (int jn = 0; jn < nodes; ++jn)
+            for (int kc = 0; kc < nkc; ++kc) wdesc[wi++] = d | (kc << 4) | (jn << 12) | (gq << 24);
+      }
     }
     dt[DT_WSTART + L + 1] = wsum;
     s_flags[0] = 0;
@@ -222,72 +234,88 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
       }
     }
   };
+  // per-row offsets of every block of step t's record (from the tables in slot t % 3),
+  // computed by one warp: first the block offsets and row strides of every slab leaf
+  // (one lane per leaf), then one multiply-add per (row, depth)
+  auto build_rowoff = [&](long long t) {
+    if (t >= total_steps) return;
+    int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff[t & 1]);
+    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
+    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
+    int* boff = reinterpret_cast<int*>(sm + a.o_boff);          // [nl][L+1]
+    int* brs = boff + nl * (L + 1);                             // [nl][L+1]
+    for (int j = lane; j < nl; j += 32) {
+      const int lam = lam0 + j;
+      const int sl = s_sz[lam];
+      int o = (int)(sro[j] - sro[0]);
+      boff[j * (L + 1)] = o;
+      brs[j * (L + 1)] = lf;
+      o += lf * lf;
+      for (int d = 1; d <= L; ++d) {
+        int r;
+        if (d <= dC) r = trk[d - 1];
+        else {
+          const int q = d - dC;
+          r = trk[dC + (1 << q) - 2 + ((lam >> (L - d)) - (vc << q))];
+        }
+        const int rs = row_stride(r);
+        boff[j * (L + 1) + d] = o;
+        brs[j * (L + 1) + d] = rs;
+        o += sl * rs;
+      }
+    }
+    __syncwarp();
+    for (int e = lane; e < ns * (L + 1); e += 32) {
+      const int i = e % ns, d = e / ns;
+      const int lam = s_leafnode[i];
+      const int j = lam - lam0;
+      const int ai = lo_c + i - s_lo[lam];
+      rowoff[d * SM + i] = boff[j * (L + 1) + d] + ai * brs[j * (L + 1) + d];
+    }
+    __syncwarp();
+  };
+  // warp 0: the bulk copy of step t's factor record and cp.async of its update vectors
   auto produce = [&](long long t) {
-    if (warp != 0) return;
-    if (t < total_steps) {
-      const int s = (int)(t % nsteps);
-      const int m = step_layer(t);
-      const int slot = (int)(t & 1);
-      int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff[slot]);
-      const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
-      const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
-      for (int i = lane; i < ns; i += 32) {
-        const int lam = s_leafnode[i];
-        const int j = lam - lam0;
-        const int sl = s_sz[lam], ai = lo_c + i - s_lo[lam];
-        int o = (int)(sro[j] - sro[0]);
-        rowoff[i] = o + ai * lf;
-        o += lf * lf;
-        for (int d = 1; d <= L; ++d) {
-          int r;
-          if (d <= dC) r = trk[d - 1];
-          else {
-            const int dd = d - dC;
-            r = trk[dC + (1 << dd) - 2 + ((lam >> (L - d)) - (vc << dd))];
-          }
-          const int rs = row_stride(r);
-          rowoff[d * SM + i] = o + ai * rs;
-          o += sl * rs;
+    if (warp != 0 || t >= total_steps) return;
+    const int s = (int)(t % nsteps);
+    const int m = step_layer(t);
+    const int slot = (int)(t & 1);
+    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
+    {
+      const int grp = team + (int)(t / nsteps) * a.nteams;
+      const int g0 = grp * G;
+      const int gcnt = (a.nrhs - g0) < G ? (a.nrhs - g0) : G;
+      const bool fwd = s < n;
+      unsigned char* vin = sm + a.o_vin[slot];
+      c128* vn = reinterpret_cast<c128*>(sm + a.o_vn[slot]);
+      const int mn = (fwd && m < n - 1) ? m + 1 : m;
+      for (int i = lane; i < ns; i += 32) cp_async16(vn + i, a.north + (long long)mn * n + lo_c + i);
+      if (fwd && m < n - 1) {
+        c128* vr = reinterpret_cast<c128*>(vin);
+        for (int e = lane; e < gcnt * ns; e += 32) {
+          const int g = e / ns, i = e % ns;
+          cp_async16(vr + g * SM + i, a.r + (long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i);
+        }
+      } else if (!fwd) {
+        Cx<R>* vw = reinterpret_cast<Cx<R>*>(vin);
+        for (int e = lane; e < gcnt * ns; e += 32) {
+          const int g = e / ns, i = e % ns;
+          const Cx<R>* src = a.w + (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
+          if (sizeof(Cx<R>) == 16) cp_async16(vw + g * SM + i, src);
+          else cp_async8(vw + g * SM + i, src);
         }
       }
-      // vectors for the update of step t
-      {
-        const int grp = team + (int)(t / nsteps) * a.nteams;
-        const int g0 = grp * G;
-        const int gcnt = (a.nrhs - g0) < G ? (a.nrhs - g0) : G;
-        const bool fwd = s < n;
-        unsigned char* vin = sm + a.o_vin[slot];
-        c128* vn = reinterpret_cast<c128*>(sm + a.o_vn[slot]);
-        const int mn = (fwd && m < n - 1) ? m + 1 : m;
-        for (int i = lane; i < ns; i += 32) cp_async16(vn + i, a.north + (long long)mn * n + lo_c + i);
-        if (fwd && m < n - 1) {
-          c128* vr = reinterpret_cast<c128*>(vin);
-          for (int e = lane; e < gcnt * ns; e += 32) {
-            const int g = e / ns, i = e % ns;
-            cp_async16(vr + g * SM + i, a.r + (long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i);
-          }
-        } else if (!fwd) {
-          Cx<R>* vw = reinterpret_cast<Cx<R>*>(vin);
-          for (int e = lane; e < gcnt * ns; e += 32) {
-            const int g = e / ns, i = e % ns;
-            const Cx<R>* src = a.w + (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
-            if (sizeof(Cx<R>) == 16) cp_async16(vw + g * SM + i, src);
-            else cp_async8(vw + g * SM + i, src);
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) {
-        unsigned bytes = (unsigned)((sro[nl] - sro[0]) * (long long)sizeof(Cx<R>));
-        unsigned long long* mb = &mbar[slot];
-        if (bytes > a.stage_bytes || bytes == 0) {
-          if (bytes > a.stage_bytes) report_error(a.status, HSWEEP_ERR_ARG, m);
-          mbar_arrive(mb);      // complete the phase without data
-        } else {
-          fence_proxy_async();
-          mbar_expect_tx(mb, bytes);
-          bulk_g2s(sm + a.o_stage[slot], a.pack + (long long)m * a.pack_stride + sro[0], bytes, mb);
-        }
+    }
+    if (lane == 0) {
+      unsigned bytes = (unsigned)((sro[nl] - sro[0]) * (long long)sizeof(Cx<R>));
+      unsigned long long* mb = &mbar[slot];
+      if (bytes > a.stage_bytes || bytes == 0) {
+        if (bytes > a.stage_bytes) report_error(a.status, HSWEEP_ERR_ARG, m);
+        mbar_arrive(mb);      // complete the phase without data
+      } else {
+        fence_proxy_async();
+        mbar_expect_tx(mb, bytes);
+        bulk_g2s(sm + a.o_stage[slot], a.pack + (long long)m * a.pack_stride + sro[0], bytes, mb);
       }
     }
   };
@@ -301,6 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
     produce(0);          // its vectors complete with the first wait of step 0
     cp_async_commit();
   }
+  if (warp == 0) build_rowoff(0);
   __syncthreads();
   long long t = 0;
   for (int grp = team; grp < a.ngroups; grp += a.nteams) {
@@ -329,6 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
         produce(t + 1);
         load_tables(t + 2);
         cp_async_commit();
+        // the next step's per-row offsets, while the other warps reduce
+        build_rowoff(t + 1);
       }
       {
         long long spins = 0;
@@ -344,7 +375,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
       const Cx<R>* st = reinterpret_cast<const Cx<R>*>(sm + a.o_stage[slot]);
       const int* rowoff = reinterpret_cast<const int*>(sm + a.o_rowoff[slot]);
       const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
-      __syncthreads();
+      // no block barrier here: every thread waited on the stage's mbarrier itself; the
+      // step's other inputs were completed before the previous step's last barrier, and
+      // the update's vectors are ordered by the barrier after the gather
       const bool ok = s_flags[0] == 0;
 
       // ---- 1. reductions q_v[k][g] = sum_i F_v[i, k] x[i][g] ---------------------------
@@ -353,15 +386,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
       //   with log2(32/KW) shuffles.
       if (ok) {
         const int wtot = dt[DT_WSTART + L + 1];
+        const int* wdesc = reinterpret_cast<const int*>(sm + a.o_wdesc);
         for (int wi = cw; wi < wtot; wi += ncw) {
-          int d = 1;
-          while (dt[DT_WSTART + d + 1] <= wi) ++d;
+          const int desc = wdesc[wi];
+          const int d = desc & 15, kc = (desc >> 4) & 255, jn = (desc >> 12) & 4095, gq = desc >> 24;
           const int kw = dt[DT_KW + d], nodes = dt[DT_NODES + d], qcap = dt[DT_QCAP + d];
-          const int nkc = (qcap + kw - 1) / kw;
-          const int item = wi - dt[DT_WSTART + d];
-          const int kc = item % nkc;
-          const int rest = item / nkc;
-          const int jn = rest % nodes, gq = rest / nodes;
           const int kl = lane % kw, rl = lane / kw, rw = 32 / kw;
           const int k = kc * kw + kl;
           int r, rb, re;
@@ -381,6 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
           if (k < r) {
             const int* ro_d = rowoff + d * SM;
             const Cx<R>* xq = x + gq * GC;
+#pragma unroll 4
             for (int i = rb + rl; i < re; i += rw) {
               const Cx<R> f = st[ro_d[i] + k];
               const Cx<R>* xr = xq + i * G;
@@ -438,83 +468,92 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tma_kernel(TmaArgs<R> a) {
       }
       __syncthreads();
 
-      // ---- 3. expansion (partials over KS column slices) -----------------------------
+      // ---- 3. expansion y_i = D x + sum_v F_v[i, :] q_sib(v), and the sweep update ----
+      //   item (row i, RHS block gq, column slice ks): the KS slices of a row are adjacent
+      //   lanes of one warp and are summed by shuffles; the lane of slice 0 then applies
+      //   the update of Algorithm 2.6 for its row.  Meanwhile the next step's per-row
+      //   offsets are built by the same threads.
       if (ok && alive) {
-        for (int item = ctid; item < ns * GQ * a.KS; item += cnt) {
-          const int i = item % ns;
-          const int rest = item / ns;
-          const int gq = rest % GQ, ks = rest / GQ;
+        const int KS = a.KS;
+        const unsigned char* vin = sm + a.o_vin[slot];
+        const c128* vn = reinterpret_cast<const c128*>(sm + a.o_vn[slot]);
+        const int nitems = ns * GQ * KS;
+        const int nitems_r = (nitems + 31) & ~31;     // whole warps, so the shuffles are converged
+        for (int item = tid; item < nitems_r; item += blockDim.x) {
+          const bool live = item < nitems;
+          const int ks = item % KS;
+          const int rest = item / KS;
+          const int i = live ? rest % ns : 0, gq = live ? rest / ns : 0;
           const int lam = s_leafnode[i];
           Cx<R> acc[GC];
 #pragma unroll
           for (int g = 0; g < GC; ++g) acc[g] = Cx<R>(0, 0);
-          if (ks == 0) {
-            const Cx<R>* D = st + rowoff[i];
-            const Cx<R>* xb = x + (s_lo[lam] - lo_c) * G + gq * GC;
-            const int sl = s_sz[lam];
-            for (int b = 0; b < sl; ++b) {
-              const Cx<R> f = D[b];
+          if (live) {
+            {
+              const Cx<R>* D = st + rowoff[i];
+              const Cx<R>* xb = x + (s_lo[lam] - lo_c) * G + gq * GC;
+              const int sl = s_sz[lam];
+              for (int b = ks; b < sl; b += KS) {
+                const Cx<R> f = D[b];
 #pragma unroll
-              for (int g = 0; g < GC; ++g) cfma(acc[g], f, xb[b * G + g]);
-            }
-          }
-          for (int d = 1; d <= L; ++d) {
-            const Cx<R>* q;
-            int r;
-            if (d <= dC) {
-              r = trk[d - 1];
-              q = qanc + (d - 1) * a.rcap * G;
-            } else {
-              const int nodes = 1 << (d - dC);
-              const int jn = (lam >> (L - d)) - (vc << (d - dC));
-              r = trk[dC + nodes - 2 + jn];
-              q = qloc + dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * G;
-            }
-            const Cx<R>* Fr = st + rowoff[d * SM + i];
-            for (int k = ks; k < r; k += a.KS) {
-              const Cx<R> f = Fr[k];
-              const Cx<R>* qk = q + k * G + gq * GC;
-#pragma unroll
-              for (int g = 0; g < GC; ++g) cfma(acc[g], f, qk[g]);
-            }
-          }
-          Cx<R>* yp = ypart + (ks * SM + i) * G + gq * GC;
-#pragma unroll
-          for (int g = 0; g < GC; ++g) yp[g] = acc[g];
-        }
-      }
-      __syncthreads();
-
-      // ---- 4. the sweep update (vectors prefetched into shared memory) ---------------
-      if (ok && alive) {
-        const unsigned char* vin = sm + a.o_vin[slot];
-        const c128* vn = reinterpret_cast<const c128*>(sm + a.o_vn[slot]);
-        for (int it = ctid; it < ns * G; it += cnt) {
-          const int i = it % ns, g = it / ns;
-          Cx<R> y(0, 0);
-          for (int ks = 0; ks < a.KS; ++ks) y += ypart[(ks * SM + i) * G + g];
-          const bool valid = g < gcount;
-          const long long p = (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
-          const Cx<R> cpl = cvt<R>(vn[i]);
-          if (fwd) {
-            if (m < n - 1) {
-              Cx<R> f(0, 0);
-              if (valid) {
-                a.w[p] = y;
-                f = cvt<R>(reinterpret_cast<const c128*>(vin)[g * SM + i]);
+                for (int g = 0; g < GC; ++g) cfma(acc[g], f, xb[b * G + g]);
               }
-              xn[i * G + g] = f - cpl * y;
-            } else {
-              if (valid) a.z[p] = cvt<double>(y);
-              xn[i * G + g] = cpl * y;
             }
-          } else {
-            Cx<R> u(0, 0);
-            if (valid) {
-              u = reinterpret_cast<const Cx<R>*>(vin)[g * SM + i] - y;
-              a.z[p] = cvt<double>(u);
+            for (int d = 1; d <= L; ++d) {
+              const Cx<R>* q;
+              int r;
+              if (d <= dC) {
+                r = trk[d - 1];
+                q = qanc + (d - 1) * a.rcap * G;
+              } else {
+                const int nodes = 1 << (d - dC);
+                const int jn = (lam >> (L - d)) - (vc << (d - dC));
+                r = trk[dC + nodes - 2 + jn];
+                q = qloc + dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * G;
+              }
+              const Cx<R>* Fr = st + rowoff[d * SM + i];
+              const Cx<R>* qg = q + gq * GC;
+#pragma unroll 4
+              for (int k = ks; k < r; k += KS) {
+                const Cx<R> f = Fr[k];
+                const Cx<R>* qk = qg + k * G;
+#pragma unroll
+                for (int g = 0; g < GC; ++g) cfma(acc[g], f, qk[g]);
+              }
             }
-            if (m > 0) xn[i * G + g] = cpl * u;
+          }
+#pragma unroll
+          for (int g = 0; g < GC; ++g)
+            for (int o = 1; o < KS; o <<= 1) acc[g] += shfl_xor(acc[g], o);
+          if (live && ks == 0) {
+            const Cx<R> cpl = cvt<R>(vn[i]);
+#pragma unroll
+            for (int gg = 0; gg < GC; ++gg) {
+              const int g = gq * GC + gg;
+              const Cx<R> y = acc[gg];
+              const bool valid = g < gcount;
+              const long long p = (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
+              if (fwd) {
+                if (m < n - 1) {
+                  Cx<R> f(0, 0);
+                  if (valid) {
+                    a.w[p] = y;
+                    f = cvt<R>(reinterpret_cast<const c128*>(vin)[g * SM + i]);
+                  }
+                  xn[i * G + g] = f - cpl * y;
+                } else {
+                  if (valid) a.z[p] = cvt<double>(y);
+                  xn[i * G + g] = cpl * y;
+                }
+              } else {
+                Cx<R> u(0, 0);
+                if (valid) {
+                  u = reinterpret_cast<const Cx<R>*>(vin)[g * SM + i] - y;
+                  a.z[p] = cvt<double>(u);
+                }
+                if (m > 0) xn[i * G + g] = cpl * u;
+              }
+            }
           }
         }
       }
@@ -553,12 +592,25 @@ static size_t plan(const hsweep_s* h, int dC, int G, int KS, TmaArgs<R>& a) {
   a.o_sz = (unsigned)o; o += al(h->nnodes * sizeof(int), 16);
   a.o_leafnode = (unsigned)o; o += al(slab_max * sizeof(int), 16);
   a.o_dtab = (unsigned)o; o += al(DT_SIZE * sizeof(int), 16);
+  {
+    long long wtot = 0;
+    for (int d = 1; d <= h->L; ++d) {
+      const int rows = d <= dC ? slab_max : h->tree.maxsz(d);
+      const int nodes = d <= dC ? 1 : (1 << (d - dC));
+      const int qcap = d <= dC ? rcap : std::min(rows, rcap);
+      int kw = 1;
+      const int kwmax = d <= dC ? 8 : 16;
+      while (kw < qcap && kw < kwmax) kw <<= 1;
+      wtot += (long long)nodes * ((qcap + kw - 1) / kw) * (G <= 5 ? 1 : G / 4);
+    }
+    a.o_wdesc = (unsigned)o; o += al((size_t)wtot * sizeof(int), 16);
+  }
+  a.o_boff = (unsigned)o; o += al((size_t)2 * nl * (h->L + 1) * sizeof(int), 16);
   for (int b = 0; b < 2; ++b) { a.o_x[b] = (unsigned)o; o += al((size_t)slab_max * G * es, 16); }
   a.o_qanc = (unsigned)o; o += al((size_t)std::max(1, dC) * rcap * G * es, 16);
   long long qloc = 0;
   for (int d = dC + 1; d <= h->L; ++d) qloc += (long long)(1 << (d - dC)) * std::min(h->tree.maxsz(d), rcap) * G;
   a.o_qloc = (unsigned)o; o += al((size_t)std::max(1LL, qloc) * es, 16);
-  a.o_ypart = (unsigned)o; o += al((size_t)KS * slab_max * G * es, 16);
   a.o_mbar = (unsigned)o; o += 16;
   a.o_flags = (unsigned)o; o += 16;
   a.stage_bytes = (unsigned)stage;
@@ -606,7 +658,7 @@ static TmaConfig choose_tma(const hsweep_s* h, int nrhs) {
     const bool grid = C > 16;
     for (int G : {8, 5, 4, 2, 1}) {
       if (G_pref > 0 && G != G_pref) continue;
-      for (int KS : {4, 2, 1}) {
+      for (int KS : {8}) {
         TmaArgs<R> a;
         const size_t smem = plan<R>(h, dC, G, KS, a);
         if (smem > cap) continue;
