@@ -179,6 +179,27 @@ def run_cpu_sample_subprocess(budget_s, applies_per_solve):
 
 
 # ---------------------------------------------------------------------------------------
+def rank_sources(w, rank):
+    """The batch of right-hand sides of one rank, (nrhs, n*n): rank 0 solves the workload's
+    own sources, every other rank the same number of point sources at its own seed."""
+    n, pml, F = w["n"], w["pml"], w["f"]
+    if rank > 0:
+        pts = synth.source_positions(n, F.shape[0], pml, 100 + rank)
+        F = np.stack([synth.source_delta(n, p) for p in pts])
+    return F.reshape(F.shape[0], n * n)
+
+
+def max_over_ranks(ms, device=None):
+    """Largest value over the ranks of the default process group (the job's time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,12 +240,8 @@ def main():
 
     w = synth.workload(args.workload)
     n, omega, pml, eps = w["n"], w["omega"], w["pml"], w["eps_H"]
-    F = w["f"]
-    if rank > 0:   # every rank solves its own batch of sources
-        pts = synth.source_positions(n, F.shape[0], pml, 100 + rank)
-        F = np.stack([synth.source_delta(n, p) for p in pts])
+    F = rank_sources(w, rank)
     nrhs = F.shape[0]
-    F = F.reshape(nrhs, n * n)
     dev = torch.device("cuda", local)
     c_d = torch.tensor(w["c"], device=dev)
     f_d = torch.tensor(F, device=dev)
@@ -265,11 +282,7 @@ def main():
     h.profile(False)
     launches, sweeps, sweep_ms = h.stats(reset=True)
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = t.item()
+    t_max = max_over_ranks(ms, dev if world > 1 else None)
     total_solves = nrhs * args.steps * world
     value = total_solves / (t_max / 1e3)
 
@@ -289,11 +302,7 @@ def main():
         u_h.copy_(u_d, non_blocking=True)
     e3.record(stream)
     barrier()
-    ms_e2e = e2.elapsed_time(e3)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = t.item()
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dev if world > 1 else None)
     e2e_value = total_solves / (ms_e2e / 1e3)
 
     # roofline of the dominant kernel (the sweep apply), from the live CUDA-event timing
