@@ -1,0 +1,890 @@
+// The apply z = M r of Algorithm 2.6 by teams of CTAs synchronised through step flags.
+//
+// A team of C = 2^dC CTAs carries G right-hand sides through the 2n-1 dependent
+// hmatvecs of the forward and backward sweeps; CTA c owns the rows of the depth-dC tree
+// node vc = 2^dC + c (its slab).  Every CTA of the grid is resident (cooperative launch,
+// one CTA per SM), so teams need no thread-block cluster and the whole GPU can be used.
+// One step (one layer m, one hmatvec y = T~_m x of Section 2.4 plus the update of
+// Algorithm 2.6) runs as:
+//   0. the layer's factor record for the slab (leaf-major packed layout, pack.cu) is
+//      already in shared memory: warp 0 issued its bulk copy one step ahead (mbarrier);
+//   1. partial sums q_v = F_v^t x over the slab's rows for the ancestors v at depths
+//      1..dC (their rows span several CTAs), written to L2;
+//   2. the CTA publishes "step t done" in its flag (release) and computes the reductions
+//      of its own subtree (depths > dC) while warp 0 waits for the flags of the other
+//      CTAs of the team (acquire, bounded spin);
+//   3. gather: the sums over the sibling subtree of every ancestor, read from L2;
+//   4. expansion y_i = D x + sum_v F_v[i, :] q_sib(v): eight lanes per row, each over
+//      every eighth column, all G right-hand sides in registers;
+//   5. the update of Algorithm 2.6 for (row, right-hand side) pairs, one per thread,
+//      with coalesced global reads (prefetched at the start of the step) and writes;
+//      the per-row offsets of the next step's record.
+// Reductions are warp-items (node, eight columns): lane = (column, one of four row
+// subsets), all G right-hand sides per lane, combined by shuffles; warps take items
+// from a shared counter.  Vectors in shared memory (x, q, y) are rows of G entries with
+// a padded stride, read as 16-byte pairs where G is even.  In complex64 the
+// multiply-adds use the paired FP32 instruction fma.rn.f32x2: with a = sum (Re f) x and
+// b = sum (Im f) x, f x = (Re a - Im b, Im a + Re b).
+#include <type_traits>
+#include "handle.h"
+#include "tma.cuh"
+
+namespace {
+
+using namespace tma;
+
+constexpr int kThreads = 512;
+constexpr int kKS = 8;                      // expansion: lanes (column slices) per row
+constexpr int kKW = 8;                      // reduction: column lanes per warp-item
+constexpr int kUPT = 2;                     // update pairs per thread (slab rows x G <= 1024)
+constexpr long long kWaitLimit = 1LL << 22; // bounded waits (about a second)
+
+typedef unsigned long long u64;
+
+// padded row stride (entries) of the shared vector arrays: conflict-free reads of one
+// row per lane group, 16-byte aligned rows where pairs are read together
+template <typename R>
+__host__ __device__ constexpr int vstride(int G) {
+  return sizeof(R) == 4 ? (G % 4 == 0 ? G + 2 : G) : (G % 2 == 0 ? G + 1 : G);
+}
+
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void fma2(u64& acc, u64 a, u64 b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// complex multiply-accumulate in the storage precision
+template <typename R> struct Mac;
+template <> struct Mac<float> {
+  struct A { u64 a, b; };          // a = sum Re(f) x, b = sum Im(f) x  (x as (re, im))
+  struct F { u64 rr, ii; };        // (Re f, Re f), (Im f, Im f)
+  typedef u64 X;
+  static __device__ __forceinline__ void zero(A& s) { s.a = 0ull; s.b = 0ull; }
+  static __device__ __forceinline__ F f(const Cx<float>* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    F r;
+    r.rr = pk2(v.x, v.x);
+    r.ii = pk2(v.y, v.y);
+    return r;
+  }
+  static __device__ __forceinline__ void mac(A& s, const F& f, X x) { fma2(s.a, f.rr, x); fma2(s.b, f.ii, x); }
+  static __device__ __forceinline__ Cx<float> get(const A& s) {
+    float ar, ai, br, bi;
+    upk2(s.a, ar, ai);
+    upk2(s.b, br, bi);
+    return Cx<float>(ar - bi, ai + br);
+  }
+};
+template <> struct Mac<double> {
+  typedef Cx<double> A, F, X;
+  static __device__ __forceinline__ void zero(A& s) { s = Cx<double>(0.0, 0.0); }
+  static __device__ __forceinline__ F f(const Cx<double>* p) { return *p; }
+  static __device__ __forceinline__ void mac(A& s, const F& f, X x) { cfma(s, f, x); }
+  static __device__ __forceinline__ Cx<double> get(const A& s) { return s; }
+};
+
+// the G entries of one vector row (16-byte pairs for complex64 rows of even length)
+template <typename R, int G>
+__device__ __forceinline__ void load_row(const Cx<R>* p, typename Mac<R>::X (&v)[G]) {
+  if constexpr (std::is_same<R, float>::value && G % 2 == 0) {
+#pragma unroll
+    for (int g = 0; g < G; g += 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p + g);
+      v[g] = t.x;
+      v[g + 1] = t.y;
+    }
+  } else if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = *reinterpret_cast<const u64*>(p + g);
+  } else {
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = p[g];
+  }
+}
+
+template <typename R>
+struct FlagArgs {
+  int n, L, leaf, nnodes, dC, C, nteams, nrhs, ngroups, slab_max, nl, rcap;
+  long long N, pack_stride;
+  unsigned stage_bytes;
+  const int* lo;
+  const int* sz;
+  const int* rank;
+  const long long* recoff;
+  const Cx<R>* pack;
+  const c128* north;
+  const c128* r;
+  c128* z;
+  Cx<R>* w;
+  Cx<R>* xch;          // ancestors' partial sums: [2][nteams][C][dC][rcap][G]
+  int* status;
+  unsigned* flags;     // [nteams * C], zero at launch
+  // shared-memory plan (byte offsets)
+  unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_btab, o_x[2],
+      o_qanc, o_qloc, o_mbar, o_flags;
+};
+
+// per-depth table columns in shared memory (16 ints each)
+enum { DT_NODES = 0, DT_QCAP = 16, DT_WSTART = 32, DT_QBASE = 48, DT_SIZE = 64 };
+
+// Reduction of one warp-item: lane (column k, row subset rl) sums rows rb + rl,
+// rb + rl + 4, ... < re of column k for all G right-hand sides.
+template <typename R, int G, int GS>
+__device__ __forceinline__ void reduce_col(const Cx<R>* __restrict__ st, const int* __restrict__ ro_d,
+                                           const Cx<R>* __restrict__ x, int rb, int re, int rl, int k,
+                                           Cx<R> (&out)[G]) {
+  using M = Mac<R>;
+  typename M::A acc[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) M::zero(acc[g]);
+#pragma unroll 4
+  for (int i = rb + rl; i < re; i += 32 / kKW) {
+    const typename M::F f = M::f(st + ro_d[i] + k);
+    typename M::X xv[G];
+    load_row<R, G>(x + i * GS, xv);
+#pragma unroll
+    for (int g = 0; g < G; ++g) M::mac(acc[g], f, xv[g]);
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) out[g] = M::get(acc[g]);
+}
+
+// Expansion of one row against one vector block: columns k = kbeg, kbeg + kKS, ...
+// < kend of the row F, vectors V[k * GS + g].
+template <typename R, int G, int GS>
+__device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const Cx<R>* __restrict__ F,
+                                           const Cx<R>* __restrict__ V, int kbeg, int kend) {
+  using M = Mac<R>;
+#pragma unroll 2
+  for (int k = kbeg; k < kend; k += kKS) {
+    const typename M::F f = M::f(F + k);
+    typename M::X v[G];
+    load_row<R, G>(V + k * GS, v);
+#pragma unroll
+    for (int g = 0; g < G; ++g) M::mac(acc[g], f, v[g]);
+  }
+}
+
+template <typename R, int G>
+__global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  using M = Mac<R>;
+  constexpr int GS = vstride<R>(G);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = a.n, L = a.L, dC = a.dC, nl = a.nl, lf = a.leaf, SM = a.slab_max;
+  const int team = blockIdx.x / a.C, c = blockIdx.x % a.C;
+  const int vc = (1 << dC) + c;
+  const int lam0 = vc << (L - dC);          // first leaf node of the slab
+  const int jglob0 = lam0 - (1 << L);       // its leaf index
+  const int L1 = L + 1;
+
+  int* s_lo = reinterpret_cast<int*>(sm + a.o_lo);
+  int* s_sz = reinterpret_cast<int*>(sm + a.o_sz);
+  int* s_leafnode = reinterpret_cast<int*>(sm + a.o_leafnode);
+  int* dt = reinterpret_cast<int*>(sm + a.o_dtab);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + a.o_mbar);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(sm + a.o_flags);
+  int* s_ctr = reinterpret_cast<int*>(sm + a.o_flags) + 1;     // reduction item counters [2]
+  Cx<R>* qanc = reinterpret_cast<Cx<R>*>(sm + a.o_qanc);
+  Cx<R>* qloc = reinterpret_cast<Cx<R>*>(sm + a.o_qloc);
+  // per (slab leaf j, depth d): block offset, row stride, rank, vector block (shared byte offset)
+  int* boff = reinterpret_cast<int*>(sm + a.o_btab);
+  int* brs = boff + nl * L1;
+  int* erk = brs + nl * L1;
+  int* evo = erk + nl * L1;
+  unsigned* tflags = a.flags + (long long)team * a.C;
+
+  for (int v = tid; v < a.nnodes; v += kThreads) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
+  __syncthreads();
+  const int lo_c = s_lo[vc], ns = s_sz[vc];
+  if (tid == 0) {
+    // reduction warp-items per depth: (node, chunk of kKW columns); ancestors first
+    int wsum = 0, qb = 0;
+    for (int d = 1; d <= L; ++d) {
+      const int rows = d <= dC ? ns : (n + (1 << d) - 1) >> d;
+      const int nodes = d <= dC ? 1 : (1 << (d - dC));
+      const int qcap = d <= dC ? a.rcap : min(rows, a.rcap);
+      dt[DT_NODES + d] = nodes;
+      dt[DT_QCAP + d] = qcap;
+      dt[DT_WSTART + d] = wsum;
+      wsum += nodes * ((qcap + kKW - 1) / kKW);
+      dt[DT_QBASE + d] = qb;
+      if (d > dC) qb += nodes * qcap * GS;
+    }
+    dt[DT_WSTART + L + 1] = wsum;
+    int* wdesc = reinterpret_cast<int*>(sm + a.o_wdesc);
+    int wi = 0;
+    for (int d = 1; d <= L; ++d) {
+      const int nodes = dt[DT_NODES + d], qcap = dt[DT_QCAP + d];
+      const int nkc = (qcap + kKW - 1) / kKW;
+      for (int jn = 0; jn < nodes; ++jn)
+        for (int kc = 0; kc < nkc; ++kc) wdesc[wi++] = d | (kc << 4) | (jn << 12);
+    }
+    *s_fail = 0;
+    s_ctr[0] = 0;
+    s_ctr[1] = 0;
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < ns; i += kThreads) {
+    int v = vc;
+    for (int d = dC; d < L; ++d) v = 2 * v + ((lo_c + i) >= s_lo[2 * v + 1] ? 1 : 0);
+    s_leafnode[i] = v;
+  }
+  __syncthreads();
+
+  const int nsteps = 2 * n - 1;
+  const int ngroups_team = a.ngroups > team ? (a.ngroups - 1 - team) / a.nteams + 1 : 0;
+  const long long total_steps = (long long)ngroups_team * nsteps;
+
+  auto step_layer = [&](long long t) {
+    const int s = (int)(t % nsteps);
+    return s < n ? s : 2 * n - 2 - s;
+  };
+  // warp 0: cp.async of the ranks of the slab's nodes and the record offsets of step t
+  // (slot t % 3, two steps ahead)
+  auto load_tables = [&](long long t) {
+    if (t >= total_steps) return;
+    const int m = step_layer(t);
+    const int slot3 = (int)(t % 3);
+    int* trk = reinterpret_cast<int*>(sm + a.o_trk[slot3]);
+    long long* sro = reinterpret_cast<long long*>(sm + a.o_ro[slot3]);
+    const int* rk = a.rank + (long long)m * a.nnodes;
+    const long long* ro = a.recoff + (long long)m * ((long long)(1 << L) + 1);
+    const int nloc = 2 * nl - 2;
+    for (int q = lane; q < dC + nloc + nl + 1; q += 32) {
+      if (q < dC) {
+        cp_async4(trk + q, rk + (vc >> (dC - 1 - q)));
+      } else if (q < dC + nloc) {
+        const int li = q - dC;
+        int dd = 1;
+        while ((1 << (dd + 1)) - 2 <= li) ++dd;
+        cp_async4(trk + q, rk + (vc << dd) + (li - ((1 << dd) - 2)));
+      } else {
+        const int j = q - dC - nloc;
+        cp_async8(sro + j, ro + jglob0 + j);
+      }
+    }
+  };
+  // all threads: per (slab leaf, depth) block of step t's record its offset, row stride,
+  // rank and the shared-memory vector block the expansion multiplies it with
+  auto build_btab = [&](long long t) {
+    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
+    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
+    auto rank_at = [&](int lam, int d) {
+      return d <= dC ? trk[d - 1] : trk[dC + (1 << (d - dC)) - 2 + ((lam >> (L - d)) - (vc << (d - dC)))];
+    };
+    for (int e = tid; e < nl * L1; e += kThreads) {
+      const int j = e / L1, d = e % L1;
+      const int lam = lam0 + j;
+      const int sl = s_sz[lam];
+      int o = (int)(sro[j] - sro[0]);
+      if (d > 0) {
+        o += lf * lf;
+        for (int dd = 1; dd < d; ++dd) o += sl * row_stride(rank_at(lam, dd));
+      }
+      boff[e] = o;
+      if (d == 0) {
+        brs[e] = lf;
+        erk[e] = sl;
+        evo[e] = 0;
+      } else {
+        const int r = rank_at(lam, d);
+        brs[e] = row_stride(r);
+        erk[e] = r;
+        if (d <= dC) {
+          evo[e] = (int)a.o_qanc + (int)sizeof(Cx<R>) * ((d - 1) * a.rcap * GS);
+        } else {
+          const int jn = (lam >> (L - d)) - (vc << (d - dC));
+          evo[e] = (int)a.o_qloc + (int)sizeof(Cx<R>) * (dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * GS);
+        }
+      }
+    }
+  };
+  // all threads: the per-row offsets of every block of the record of the step whose
+  // block tables were built last
+  auto build_rows = [&]() {
+    int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff);
+    for (int e = tid; e < ns * L1; e += kThreads) {
+      const int i = e % ns, d = e / ns;
+      const int lam = s_leafnode[i];
+      const int j = lam - lam0;
+      rowoff[d * SM + i] = boff[j * L1 + d] + (lo_c + i - s_lo[lam]) * brs[j * L1 + d];
+    }
+  };
+  // warp 0, lane 0: the bulk copy of step t's factor record into stage t & 1
+  auto produce = [&](long long t) {
+    if (t >= total_steps || lane != 0) return;
+    const int m = step_layer(t);
+    const int slot = (int)(t & 1);
+    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
+    const unsigned bytes = (unsigned)((sro[nl] - sro[0]) * (long long)sizeof(Cx<R>));
+    unsigned long long* mb = &mbar[slot];
+    if (bytes > a.stage_bytes || bytes == 0) {
+      if (bytes > a.stage_bytes) report_error(a.status, HSWEEP_ERR_ARG, m);
+      mbar_arrive(mb);      // complete the phase without data
+    } else {
+      fence_proxy_async();
+      mbar_expect_tx(mb, bytes);
+      bulk_g2s(sm + a.o_stage[slot], a.pack + (long long)m * a.pack_stride + sro[0], bytes, mb);
+    }
+  };
+
+  if (warp == 0) {
+    load_tables(0);
+    load_tables(1);
+    cp_async_commit();
+    cp_async_wait0();
+    __syncwarp();
+    produce(0);
+  }
+  __syncthreads();
+  if (total_steps > 0) build_btab(0);
+  __syncthreads();
+  if (total_steps > 0) build_rows();
+  __syncthreads();
+
+  long long issued = total_steps > 0 ? 1 : 0;   // bulk copies issued (steps 0 .. issued-1)
+  long long t = 0;
+  for (; t < total_steps; ++t) {
+    const int s = (int)(t % nsteps);
+    const int grp = team + (int)(t / nsteps) * a.nteams;
+    const int g0 = grp * G;
+    const int gcount = (a.nrhs - g0) < G ? (a.nrhs - g0) : G;
+    const bool fwd = s < n;
+    const int m = fwd ? s : 2 * n - 2 - s;
+    const int slot = (int)(t & 1);
+    Cx<R>* x = reinterpret_cast<Cx<R>*>(sm + a.o_x[s & 1]);
+    Cx<R>* xn = reinterpret_cast<Cx<R>*>(sm + a.o_x[(s + 1) & 1]);
+    // the expansion's result y is held in the next step's x buffer: the update reads
+    // y[i][g] and then writes x_next[i][g] in the same thread
+    Cx<R>* ybuf = xn;
+    if (s == 0) {     // a new group: x = r restricted to layer 0 and the slab's rows
+      for (int it = tid; it < ns * G; it += kThreads) {
+        const int i = it / G, g = it % G;
+        Cx<R> v(0, 0);
+        if (g < gcount) v = cvt<R>(a.r[(long long)(g0 + g) * a.N + lo_c + i]);
+        x[i * GS + g] = v;
+      }
+      __syncthreads();
+    }
+    // the update's global inputs for this thread's (row, right-hand side) pairs
+    c128 pin[kUPT], pcpl[kUPT];
+    Cx<R> pw[kUPT];
+    {
+      const int mn = (fwd && m < n - 1) ? m + 1 : m;
+#pragma unroll
+      for (int u = 0; u < kUPT; ++u) {
+        const int p = tid + u * kThreads;
+        pin[u] = c128(0.0, 0.0);
+        pw[u] = Cx<R>(0, 0);
+        pcpl[u] = c128(0.0, 0.0);
+        if (p < ns * G) {
+          const int i = p % ns, g = p / ns;
+          pcpl[u] = a.north[(long long)mn * n + lo_c + i];
+          if (g < gcount) {
+            if (fwd && m < n - 1) pin[u] = a.r[(long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i];
+            else if (!fwd) pw[u] = a.w[(long long)(g0 + g) * a.N + (long long)m * n + lo_c + i];
+          }
+        }
+      }
+    }
+    {   // the stage of step t
+      long long spins = 0;
+      const unsigned parity = (unsigned)((t >> 1) & 1);
+      while (!mbar_try_wait(&mbar[slot], parity)) {
+        if (++spins > kWaitLimit) {
+          report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
+          *s_fail = 1;
+          break;
+        }
+      }
+    }
+    const Cx<R>* st = reinterpret_cast<const Cx<R>*>(sm + a.o_stage[slot]);
+    const int* rowoff = reinterpret_cast<const int*>(sm + a.o_rowoff);
+    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
+    const int* wdesc = reinterpret_cast<const int*>(sm + a.o_wdesc);
+    const int par = (int)(t & 1);
+
+    // reduction warp-items [wb, we), taken from the shared counter s_ctr[which]
+    auto reduce_items = [&](int wb, int we, int which) {
+      const int kl = lane % kKW, rl = lane / kKW;
+      for (;;) {
+        int wi = 0;
+        if (lane == 0) wi = atomicAdd(&s_ctr[which], 1);
+        wi = __shfl_sync(0xffffffffu, wi, 0) + wb;
+        if (wi >= we) break;
+        const int desc = wdesc[wi];
+        const int d = desc & 15, kc = (desc >> 4) & 255, jn = (desc >> 12) & 4095;
+        const int nodes = dt[DT_NODES + d], qcap = dt[DT_QCAP + d];
+        const int k = kc * kKW + kl;
+        int r, rb, re;
+        if (d <= dC) {
+          r = trk[d - 1];
+          rb = 0;
+          re = ns;
+        } else {
+          const int v = (vc << (d - dC)) + jn;
+          r = trk[dC + nodes - 2 + jn];
+          rb = s_lo[v] - lo_c;
+          re = rb + s_sz[v];
+        }
+        if (kc * kKW >= r) continue;           // the whole item is past the rank
+        Cx<R> out[G];
+        reduce_col<R, G, GS>(st, rowoff + d * SM, x, rb, re, rl, min(k, r - 1), out);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+          for (int o = kKW; o < 32; o <<= 1) out[g] += shfl_xor(out[g], o);
+        if (rl == 0 && k < r && k < qcap) {
+          if (d <= dC) {
+            Cx<R>* dst = a.xch + ((((long long)par * a.nteams + team) * a.C + c) * dC + (d - 1)) * a.rcap * G + k * G;
+#pragma unroll
+            for (int g = 0; g < G; ++g) st_cg(dst + g, out[g]);
+          } else {
+            Cx<R>* dst = qloc + dt[DT_QBASE + d] + (jn * qcap + k) * GS;
+#pragma unroll
+            for (int g = 0; g < G; ++g) dst[g] = out[g];
+          }
+        }
+      }
+    };
+
+    // ---- 1. warp 0 issues step t + 1's bulk copy and step t + 2's tables; then all
+    //         warps compute the ancestors' partial sums --------------------------------
+    const bool ok1 = *s_fail == 0;
+    if (warp == 0) {
+      cp_async_wait0();      // the tables of step t + 1
+      __syncwarp();
+      if (ok1) {
+        produce(t + 1);
+        load_tables(t + 2);
+        cp_async_commit();
+      }
+    }
+    if (ok1) reduce_items(0, dt[DT_WSTART + dC + 1], 0);
+    if (ok1 && t + 1 < total_steps) issued = t + 2;
+    __syncthreads();
+
+    // ---- 2. publish; subtree reductions while warp 0 waits for the team ---------------
+    if (warp == 0) {
+      if (tid == 0) {
+        __threadfence();
+        st_release(tflags + c, (unsigned)(t + 1));
+      }
+      for (int cc = lane; cc < a.C; cc += 32) {
+        if (cc == c) continue;
+        long long spins = 0;
+        while (ld_acquire(tflags + cc) < (unsigned)(t + 1)) {
+          if (*(volatile int*)a.status != 0) { *s_fail = 1; break; }
+          if (++spins > kWaitLimit) {
+            report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
+            *s_fail = 1;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      __syncwarp();
+    } else if (*s_fail == 0) {
+      reduce_items(dt[DT_WSTART + dC + 1], dt[DT_WSTART + L + 1], 1);
+    }
+    __syncthreads();
+    if (*s_fail != 0) break;
+
+    // ---- 3. sums over the sibling subtree of every ancestor (all loads of a thread's
+    //         items in flight together); the next step's block tables ------------------
+    {
+      constexpr int GJ = sizeof(R) == 4 ? 3 : 1;
+      const int rg = a.rcap * G;
+      const int tot = dC * rg;
+      const long long cstride = (long long)dC * rg;
+      const Cx<R>* xb = a.xch + ((long long)par * a.nteams + team) * a.C * cstride;
+      for (int base = tid; base < tot; base += GJ * kThreads) {
+        Cx<R> vals[GJ][8];
+#pragma unroll
+        for (int j = 0; j < GJ; ++j) {
+          const int it = base + j * kThreads;
+          const int d = it < tot ? it / rg + 1 : 1;
+          const int kg = it - (d - 1) * rg;
+          const int span = 1 << (dC - d);
+          const int c0 = (((vc >> (dC - d)) ^ 1) << (dC - d)) - (1 << dC);
+          const bool use = it < tot && kg / G < trk[d - 1];
+          const Cx<R>* src = xb + (long long)(d - 1) * rg + kg + (long long)c0 * cstride;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) vals[j][u] = (use && u < span) ? ld_cg(src + u * cstride) : Cx<R>(0, 0);
+          if (use) {
+            for (int cc = 8; cc < span; ++cc) vals[j][0] += ld_cg(src + cc * cstride);   // teams over 16 CTAs
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < GJ; ++j) {
+          const int it = base + j * kThreads;
+          if (it < tot) {
+            Cx<R> acc = vals[j][0];
+#pragma unroll
+            for (int u = 1; u < 8; ++u) acc += vals[j][u];
+            const int d = it / rg + 1;
+            const int kg = it - (d - 1) * rg;
+            qanc[(d - 1) * a.rcap * GS + (kg / G) * GS + kg % G] = acc;
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- 4. expansion: lane = (row i, column slice ks) --------------------------------
+    {
+      const int nitems = ns * kKS;
+      for (int item = tid; item < ((nitems + 31) & ~31); item += kThreads) {
+        const bool live = item < nitems;
+        const int ks = item % kKS;
+        const int i = live ? item / kKS : 0;
+        const int lam = s_leafnode[i];
+        const int j = lam - lam0;
+        const int ib = s_lo[lam] - lo_c;               // first slab row of the leaf
+        typename M::A acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) M::zero(acc[g]);
+        if (live) {
+          const int* eb = erk + j * L1;
+          const int* ev = evo + j * L1;
+          expand_row<R, G, GS>(acc, st + rowoff[i], x + ib * GS, ks, eb[0]);
+          for (int d = 1; d <= L; ++d)
+            expand_row<R, G, GS>(acc, st + rowoff[d * SM + i], reinterpret_cast<const Cx<R>*>(sm + ev[d]), ks, eb[d]);
+        }
+        Cx<R> y[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          y[g] = M::get(acc[g]);
+#pragma unroll
+          for (int o = 1; o < kKS; o <<= 1) y[g] += shfl_xor(y[g], o);
+        }
+        if (live && ks == 0) {
+#pragma unroll
+          for (int g = 0; g < G; ++g) ybuf[i * GS + g] = y[g];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- 5. the update of Algorithm 2.6 for this thread's (row, rhs) pairs; the next
+    //         step's block tables ---------------------------------------------------------
+#pragma unroll
+    for (int u = 0; u < kUPT; ++u) {
+      const int p = tid + u * kThreads;
+      if (p < ns * G) {
+        const int i = p % ns, g = p / ns;
+        const bool valid = g < gcount;
+        const Cx<R> y = ybuf[i * GS + g];
+        const Cx<R> cpl = cvt<R>(pcpl[u]);
+        const long long pos = (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
+        if (fwd) {
+          if (m < n - 1) {
+            if (valid) a.w[pos] = y;
+            xn[i * GS + g] = cvt<R>(pin[u]) - cpl * y;
+          } else {
+            if (valid) a.z[pos] = cvt<double>(y);
+            xn[i * GS + g] = cpl * y;
+          }
+        } else {
+          const Cx<R> uu = valid ? pw[u] - y : Cx<R>(0, 0);
+          if (valid) a.z[pos] = cvt<double>(uu);
+          if (m > 0) xn[i * GS + g] = cpl * uu;
+        }
+      }
+    }
+    if (t + 1 < total_steps) build_btab(t + 1);
+    if (tid == 0) { s_ctr[0] = 0; s_ctr[1] = 0; }
+    __syncthreads();
+    if (t + 1 < total_steps) build_rows();
+    __syncthreads();
+  }
+  // a CTA that stopped early still owns the bulk copies it issued: wait for them
+  if (tid == 0) {
+    for (long long q = t + 1; q < issued; ++q) {
+      long long spins = 0;
+      const unsigned parity = (unsigned)((q >> 1) & 1);
+      while (!mbar_try_wait(&mbar[q & 1], parity) && ++spins <= kWaitLimit) {
+      }
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+namespace {
+
+struct FlagConfig {
+  bool ok;
+  int dC, C, G, nteams;
+  size_t smem;
+};
+
+static int ilog2f(int x) { int l = 0; while ((1 << (l + 1)) <= x) ++l; return l; }
+
+// shared-memory plan for (dC, G); returns total bytes (0 if the layout is not supported)
+template <typename R>
+static size_t plan_flag(const hsweep_s* h, int dC, int G, FlagArgs<R>& a) {
+  const size_t es = sizeof(Cx<R>);
+  const int L = h->L;
+  const int nl = 1 << (L - dC);
+  const int slab_max = h->tree.maxsz(dC);
+  const int rcap = std::max(1, h->rank_max);
+  const int GS = vstride<R>(G);
+  if (L > 14 || (long long)slab_max * G > (long long)kUPT * kThreads || h->leaf > 8) return 0;
+  auto al = [](size_t x, size_t b) { return (x + b - 1) / b * b; };
+  size_t o = 0;
+  const size_t stage = al((size_t)h->slab_bytes_max[dC], 128);
+  for (int b = 0; b < 2; ++b) { a.o_stage[b] = (unsigned)o; o += stage; }
+  a.o_rowoff = (unsigned)o; o += al((size_t)(L + 1) * slab_max * sizeof(int), 16);
+  for (int b = 0; b < 3; ++b) { a.o_trk[b] = (unsigned)o; o += al((size_t)(dC + 2 * nl) * sizeof(int), 16); }
+  for (int b = 0; b < 3; ++b) { a.o_ro[b] = (unsigned)o; o += al((size_t)(nl + 1) * sizeof(long long), 16); }
+  a.o_lo = (unsigned)o; o += al(h->nnodes * sizeof(int), 16);
+  a.o_sz = (unsigned)o; o += al(h->nnodes * sizeof(int), 16);
+  a.o_leafnode = (unsigned)o; o += al(slab_max * sizeof(int), 16);
+  a.o_dtab = (unsigned)o; o += al(DT_SIZE * sizeof(int), 16);
+  long long wtot = 0, qloc = 0;
+  for (int d = 1; d <= L; ++d) {
+    const int rows = d <= dC ? slab_max : h->tree.maxsz(d);
+    const int nodes = d <= dC ? 1 : (1 << (d - dC));
+    const int qcap = d <= dC ? rcap : std::min(rows, rcap);
+    wtot += (long long)nodes * ((qcap + kKW - 1) / kKW);
+    if (d > dC) qloc += (long long)nodes * qcap * GS;
+  }
+  a.o_wdesc = (unsigned)o; o += al((size_t)wtot * sizeof(int), 16);
+  a.o_btab = (unsigned)o; o += al((size_t)4 * nl * (L + 1) * sizeof(int), 16);
+  for (int b = 0; b < 2; ++b) { a.o_x[b] = (unsigned)o; o += al((size_t)slab_max * GS * es, 16); }
+  a.o_qanc = (unsigned)o; o += al((size_t)std::max(1, dC) * rcap * GS * es, 16);
+  a.o_qloc = (unsigned)o; o += al((size_t)std::max(1LL, qloc) * es, 16);
+  a.o_mbar = (unsigned)o; o += 16;
+  a.o_flags = (unsigned)o; o += 16;
+  a.stage_bytes = (unsigned)stage;
+  a.nl = nl;
+  a.slab_max = slab_max;
+  a.rcap = rcap;
+  return o;
+}
+
+template <typename R, int G>
+static int resident_ctas(const hsweep_s* h, size_t smem) {
+  auto kern = sweep_flag_kernel<R, G>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * h->num_sms;
+}
+
+template <typename R>
+static int resident_for(const hsweep_s* h, int G, size_t smem) {
+  switch (G) {
+    case 1: return resident_ctas<R, 1>(h, smem);
+    case 2: return resident_ctas<R, 2>(h, smem);
+    case 4: return resident_ctas<R, 4>(h, smem);
+    case 5: return resident_ctas<R, 5>(h, smem);
+    default: return resident_ctas<R, 8>(h, smem);
+  }
+}
+
+// Team size C and right-hand sides per team G: the fewest rounds of 2n-1 dependent
+// steps, a step costing a fixed latency (flag exchange, barriers) plus work that grows
+// with the slab's rows times G.
+template <typename R>
+static FlagConfig choose_flag(const hsweep_s* h, int nrhs) {
+  FlagConfig best{};
+  best.ok = false;
+  double best_cost = 1e300;
+  const size_t cap = 227 * 1024;
+  const int C_pref = h->opt.team, G_pref = h->opt.groups;
+  for (int C = 1; C <= h->nleaves && C <= h->num_sms; C *= 2) {
+    if (C_pref > 0 && C != (1 << ilog2f(C_pref))) continue;
+    const int dC = ilog2f(C);
+    for (int G : {8, 5, 4, 2, 1}) {
+      if (G_pref > 0 && G != G_pref) continue;
+      FlagArgs<R> a;
+      const size_t smem = plan_flag<R>(h, dC, G, a);
+      if (smem == 0 || smem > cap) continue;
+      const int resident = resident_for<R>(h, G, smem);
+      const int teams_cap = std::min(resident, 1024) / C;
+      if (teams_cap < 1) continue;
+      const int ngroups = (nrhs + G - 1) / G;
+      const int teams = std::min(ngroups, teams_cap);
+      const int rounds = (ngroups + teams - 1) / teams;
+      const double es = (double)sizeof(Cx<R>) / 8.0;
+      const double step = 2.5 + 0.012 * es * a.slab_max * G + 0.4 * dC + 0.01 * C;
+      const double cost = rounds * step;
+      if (cost < best_cost - 1e-9) {
+        best_cost = cost;
+        best = FlagConfig{true, dC, C, G, teams, smem};
+      }
+    }
+  }
+  return best;
+}
+
+template <typename R, int G>
+static int launch_flag(hsweep_s* h, const FlagConfig& cfg, FlagArgs<R>& a) {
+  auto kern = sweep_flag_kernel<R, G>;
+  HSW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  lc.blockDim = dim3(kThreads);
+  lc.gridDim = dim3(cfg.C * cfg.nteams);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = h->stream;
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->prof) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!h->ev_free.empty()) { *e = h->ev_free.back(); h->ev_free.pop_back(); }
+      else HSW_CUDA(cudaEventCreate(e));
+    }
+    HSW_CUDA(cudaEventRecord(e0, h->stream));
+  }
+  HSW_CUDA(cudaLaunchKernelEx(&lc, kern, a));
+  h->nlaunch += 1;
+  if (h->prof) {
+    HSW_CUDA(cudaEventRecord(e1, h->stream));
+    h->ev_sweep.push_back({e0, e1});
+  }
+  return HSWEEP_OK;
+}
+
+template <typename R>
+static int dispatch_flag(hsweep_s* h, const FlagConfig& cfg, FlagArgs<R>& a) {
+  switch (cfg.G) {
+    case 1: return launch_flag<R, 1>(h, cfg, a);
+    case 2: return launch_flag<R, 2>(h, cfg, a);
+    case 4: return launch_flag<R, 4>(h, cfg, a);
+    case 5: return launch_flag<R, 5>(h, cfg, a);
+    default: return launch_flag<R, 8>(h, cfg, a);
+  }
+}
+
+static long long al256f(long long x) { return (x + 255) / 256 * 256; }
+
+template <typename R>
+static void flag_scratch_need(const hsweep_s* h, int nrhs, const FlagConfig& cfg, long long* w_bytes,
+                              long long* x_bytes) {
+  const long long es = sizeof(Cx<R>);
+  *w_bytes = (long long)nrhs * h->N * es;
+  *x_bytes = 2LL * cfg.nteams * cfg.C * std::max(1, cfg.dC) * std::max(1, h->rank_max) * cfg.G * es;
+}
+
+template <typename R>
+static int apply_flag_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch,
+                           size_t scratch_bytes) {
+  *used = false;
+  FlagConfig cfg = choose_flag<R>(h, nrhs);
+  if (!cfg.ok) return HSWEEP_OK;
+  const size_t es = sizeof(Cx<R>);
+  long long wb, xb;
+  flag_scratch_need<R>(h, nrhs, cfg, &wb, &xb);
+  void* wptr;
+  void* xptr;
+  if (scratch) {    // caller-provided scratch: nothing is allocated
+    if ((size_t)(al256f(wb) + al256f(xb)) > scratch_bytes) return HSWEEP_ERR_ARG;
+    wptr = scratch;
+    xptr = (unsigned char*)scratch + al256f(wb);
+  } else {
+    const long long need_w = (long long)nrhs * h->N;
+    if (need_w > h->wcache_cap) {
+      hsw_release(h, h->d_wcache); h->d_wcache = nullptr; h->wcache_cap = 0;
+      int rc = hsw_alloc(h, &h->d_wcache, (size_t)need_w * es);
+      if (rc) return rc;
+      h->wcache_cap = need_w;
+    }
+    const long long need_x = xb / (long long)es;
+    if (need_x > h->xch_cap) {
+      hsw_release(h, h->d_xch); h->d_xch = nullptr; h->xch_cap = 0;
+      int rc = hsw_alloc(h, &h->d_xch, (size_t)need_x * es);
+      if (rc) return rc;
+      h->xch_cap = need_x;
+    }
+    wptr = h->d_wcache;
+    xptr = h->d_xch;
+  }
+  FlagArgs<R> a;
+  plan_flag<R>(h, cfg.dC, cfg.G, a);
+  a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.nnodes = h->nnodes; a.dC = cfg.dC; a.C = cfg.C;
+  a.nteams = cfg.nteams; a.nrhs = nrhs; a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
+  a.N = h->N; a.pack_stride = h->pack_stride;
+  a.lo = h->d_lo; a.sz = h->d_sz; a.rank = h->d_rank; a.recoff = h->d_recoff;
+  a.pack = reinterpret_cast<const Cx<R>*>(h->d_pack);
+  a.north = h->d_north; a.r = r; a.z = z;
+  a.w = reinterpret_cast<Cx<R>*>(wptr);
+  a.xch = reinterpret_cast<Cx<R>*>(xptr);
+  a.status = h->d_status; a.flags = h->d_flags;
+  const bool prof = h->prof;
+  if (scratch) h->prof = false;   // the no-allocation path creates no events
+  int rc = HSWEEP_OK;
+  if (cudaMemsetAsync(h->d_flags, 0, (size_t)cfg.nteams * cfg.C * sizeof(unsigned), h->stream) != cudaSuccess)
+    rc = HSWEEP_ERR_CUDA;
+  if (rc == HSWEEP_OK) rc = dispatch_flag<R>(h, cfg, a);
+  h->prof = prof;
+  if (rc == HSWEEP_OK) *used = true;
+  return rc;
+}
+
+static bool flag_usable(const hsweep_s* h) {
+  return h->pack_valid && !h->slab_bytes_max.empty() && h->d_flags != nullptr;
+}
+
+}  // namespace
+
+int hsw_flag_plan(hsweep_s* h, int nrhs, long long* out) {
+  FlagConfig cfg{};
+  if (flag_usable(h)) cfg = h->prec == HSWEEP_FP64 ? choose_flag<double>(h, nrhs) : choose_flag<float>(h, nrhs);
+  if (!cfg.ok) return 0;
+  out[0] = 2; out[1] = cfg.C; out[2] = cfg.G; out[3] = cfg.nteams; out[4] = 0;
+  out[5] = (long long)cfg.smem; out[6] = h->slab_bytes_max[cfg.dC]; out[7] = kKS;
+  return 1;
+}
+
+int hsw_apply_flag(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch, size_t scratch_bytes) {
+  *used = false;
+  if (!flag_usable(h)) return HSWEEP_OK;
+  if (h->prec == HSWEEP_FP64) return apply_flag_impl<double>(h, r, z, nrhs, used, scratch, scratch_bytes);
+  return apply_flag_impl<float>(h, r, z, nrhs, used, scratch, scratch_bytes);
+}
+
+size_t hsw_apply_flag_scratch_bytes(hsweep_s* h, int nrhs) {
+  if (!flag_usable(h)) return 0;
+  long long wb, xb;
+  if (h->prec == HSWEEP_FP64) {
+    FlagConfig cfg = choose_flag<double>(h, nrhs);
+    if (!cfg.ok) return 0;
+    flag_scratch_need<double>(h, nrhs, cfg, &wb, &xb);
+  } else {
+    FlagConfig cfg = choose_flag<float>(h, nrhs);
+    if (!cfg.ok) return 0;
+    flag_scratch_need<float>(h, nrhs, cfg, &wb, &xb);
+  }
+  return (size_t)(al256f(wb) + al256f(xb));
+}
