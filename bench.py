@@ -321,7 +321,7 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
     plan = h.sweep_plan(nrhs)
-    roof["kernel"] = {2: "sweep_flag_kernel", 1: "sweep_tma_kernel"}.get(plan["tma"], "sweep_kernel") + "<c64>"
+    roof["kernel"] = {2: "sweep_team_kernel", 1: "sweep_tma_kernel"}.get(plan["tma"], "sweep_kernel") + "<c64>"
     roof["plan"] = plan
     roof["launch_ms"] = avg_s * 1e3
     roof["hbm_gbs_achieved"] = bytes_ / avg_s / 1e9

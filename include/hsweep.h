@@ -71,8 +71,8 @@ typedef struct {
   int refine_max;    /* outer FP64 refinement steps in HSWEEP_MIXED (default 8) */
   int team;          /* CTAs per sweep team (power of two, 0 = automatic) */
   int groups;        /* right-hand sides per sweep team (1, 2, 4, 5 or 8; 0 = automatic) */
-  int sweep_kernel;  /* 0: automatic (default): the flag-synchronised TMA-staged sweep,
-                           else the cluster TMA-staged sweep, else the basic sweep, the
+  int sweep_kernel;  /* 0: automatic (default): the TMA-staged sweep on cooperative teams,
+                           else the TMA-staged sweep on clusters, else the basic sweep, the
                            first whose shared-memory plan fits;
                         1: the basic sweep that reads the factors from global memory;
                         2: the TMA-staged sweep on thread-block clusters (else basic) */
@@ -197,7 +197,7 @@ HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
 /*
  * The launch plan the apply would use for nrhs right-hand sides (diagnostics):
  * out[0] the sweep kernel (0: basic, 1: TMA-staged on thread-block clusters, 2: TMA-staged
- * with flag-synchronised teams), out[1] CTAs per team, out[2] right-hand sides per team,
+ * on cooperative teams exchanging tagged partial sums), out[1] CTAs per team, out[2] right-hand sides per team,
  * out[3] teams, out[4] 1 for a whole-grid team with a grid barrier, out[5] dynamic shared
  * memory per CTA in bytes, out[6] largest per-step factor record of one CTA in bytes,
  * out[7] column slices per row in the expansion (0 for the basic kernel).

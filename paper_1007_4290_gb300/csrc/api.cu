@@ -140,7 +140,6 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   TRY(hsw_alloc(h, (void**)&h->d_recoff, (size_t)n * (h->nleaves + 1) * sizeof(long long)));
   TRY(hsw_alloc(h, (void**)&h->d_status, 2 * sizeof(int)));
   TRY(hsw_alloc(h, (void**)&h->d_bar, 2 * sizeof(unsigned)));
-  TRY(hsw_alloc(h, (void**)&h->d_flags, hsweep_s::kMaxFlags * sizeof(unsigned)));
   TRYC(cudaMemcpyAsync(h->d_lo, h->tree.lo.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   TRYC(cudaMemcpyAsync(h->d_sz, h->tree.sz.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   TRYC(cudaMemcpyAsync(h->d_off, h->off.data(), h->nnodes * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
@@ -149,7 +148,6 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   TRYC(cudaMemsetAsync(h->d_recoff, 0, (size_t)n * (h->nleaves + 1) * sizeof(long long), h->stream));
   TRYC(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), h->stream));
   TRYC(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
-  TRYC(cudaMemsetAsync(h->d_flags, 0, hsweep_s::kMaxFlags * sizeof(unsigned), h->stream));
   TRYC(cudaMemcpyAsync(h->d_c, c_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   // the velocity must be finite and positive
   {
@@ -347,7 +345,7 @@ extern "C" int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
 
 extern "C" int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8) {
   if (!h || !out8 || nrhs < 1) return HSWEEP_ERR_ARG;
-  if (h->opt.sweep_kernel == 0 && hsw_flag_plan(h, nrhs, out8)) return HSWEEP_OK;
+  if (h->opt.sweep_kernel == 0 && hsw_team_plan(h, nrhs, out8)) return HSWEEP_OK;
   if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) return hsw_tma_plan(h, nrhs, out8);
   for (int i = 0; i < 8; ++i) out8[i] = 0;
   return HSWEEP_OK;

@@ -444,7 +444,7 @@ int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs) {
   if (nrhs <= 0) return HSWEEP_OK;
   if (h->opt.sweep_kernel == 0) {
     bool used = false;
-    int rc = hsw_apply_flag(h, r, z, nrhs, &used);
+    int rc = hsw_apply_team(h, r, z, nrhs, &used);
     if (rc != HSWEEP_OK || used) return rc;
   }
   if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) {
@@ -466,7 +466,7 @@ static long long align_up(long long x, long long a) { return (x + a - 1) / a * a
 size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs) {
   if (nrhs <= 0) return 0;
   if (h->opt.sweep_kernel == 0) {
-    const size_t fl = hsw_apply_flag_scratch_bytes(h, nrhs);
+    const size_t fl = hsw_apply_team_scratch_bytes(h, nrhs);
     if (fl > 0) return fl;
   }
   if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) {
@@ -524,7 +524,7 @@ int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scrat
   if (hsw_apply_scratch_bytes(h, nrhs) > bytes) return HSWEEP_ERR_ARG;
   if (h->opt.sweep_kernel == 0) {      // the same kernel hsw_apply would use
     bool used = false;
-    int rc = hsw_apply_flag(h, r, z, nrhs, &used, scratch, bytes);
+    int rc = hsw_apply_team(h, r, z, nrhs, &used, scratch, bytes);
     if (rc != HSWEEP_OK || used) return rc;
   }
   if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) {

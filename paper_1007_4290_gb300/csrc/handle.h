@@ -69,8 +69,6 @@ struct hsweep_s {
 
   int* d_status = nullptr;     // [2]
   unsigned* d_bar = nullptr;   // grid barrier words [2]
-  unsigned* d_flags = nullptr; // per-CTA step flags of the flag-synchronised sweep [kMaxFlags]
-  static constexpr int kMaxFlags = 1024;
 
   // sweep workspace
   void* d_wcache = nullptr;    // [cap][N] in storage precision
@@ -110,11 +108,11 @@ int hsw_apply_tma(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, voi
                   size_t scratch_bytes = 0);
 size_t hsw_apply_tma_scratch_bytes(hsweep_s* h, int nrhs);
 int hsw_tma_plan(hsweep_s* h, int nrhs, long long* out8);
-// sweep_flag.cu
-int hsw_apply_flag(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch = nullptr,
+// sweep_team.cu
+int hsw_apply_team(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch = nullptr,
                    size_t scratch_bytes = 0);
-size_t hsw_apply_flag_scratch_bytes(hsweep_s* h, int nrhs);
-int hsw_flag_plan(hsweep_s* h, int nrhs, long long* out8);   // 1 if the flag kernel would run
+size_t hsw_apply_team_scratch_bytes(hsweep_s* h, int nrhs);
+int hsw_team_plan(hsweep_s* h, int nrhs, long long* out8);   // 1 if the team kernel would run
 // setup.cu
 int hsw_factor(hsweep_s* h);
 void hsw_setup_free(hsweep_s* h);

@@ -1,4 +1,4 @@
-// The apply z = M r of Algorithm 2.6 by teams of CTAs synchronised through step flags.
+// The apply z = M r of Algorithm 2.6 by cooperative teams of CTAs.
 //
 // A team of C = 2^dC CTAs carries G right-hand sides through the 2n-1 dependent
 // hmatvecs of the forward and backward sweeps; CTA c owns the rows of the depth-dC tree
@@ -7,18 +7,24 @@
 // One step (one layer m, one hmatvec y = T~_m x of Section 2.4 plus the update of
 // Algorithm 2.6) runs as:
 //   0. the layer's factor record for the slab (leaf-major packed layout, pack.cu) is
-//      already in shared memory: warp 0 issued its bulk copy one step ahead (mbarrier);
+//      already in shared memory: warp 0 issued its bulk copy one step ahead (mbarrier),
+//      and now issues the next one and builds the next step's block tables;
 //   1. partial sums q_v = F_v^t x over the slab's rows for the ancestors v at depths
-//      1..dC (their rows span several CTAs), written to L2;
-//   2. the CTA publishes "step t done" in its flag (release) and computes the reductions
-//      of its own subtree (depths > dC) while warp 0 waits for the flags of the other
-//      CTAs of the team (acquire, bounded spin);
-//   3. gather: the sums over the sibling subtree of every ancestor, read from L2;
+//      1..dC (their rows span several CTAs), stored to L2 with a step tag;
+//   2. the reductions of the CTA's own subtree (depths > dC), then
+//   3. the gather: the sums over the sibling subtree of every ancestor, read from L2,
+//      re-read until every word carries the tag of this step;
 //   4. expansion y_i = D x + sum_v F_v[i, :] q_sib(v): eight lanes per row, each over
 //      every eighth column, all G right-hand sides in registers;
 //   5. the update of Algorithm 2.6 for (row, right-hand side) pairs, one per thread,
 //      with coalesced global reads (prefetched at the start of the step) and writes;
 //      the per-row offsets of the next step's record.
+// Three block barriers per step; no team-wide barrier: a CTA waits only for the
+// partial sums it reads.  The tag is the lowest bit of every 8-byte word of a partial
+// sum, equal to bit 1 of the step index: a slot (one per step parity) holds either
+// this step's value or the one from two steps before, because no CTA can run two steps
+// ahead of a CTA whose partial sums it reads.  The tag costs one bit of the stored
+// mantissa (relative 2^-23 in complex64, 2^-52 in complex128).
 // Reductions are warp-items (node, eight columns): lane = (column, one of four row
 // subsets), all G right-hand sides per lane, combined by shuffles; warps take items
 // from a shared counter.  Vectors in shared memory (x, q, y) are rows of G entries with
@@ -36,7 +42,8 @@ using namespace tma;
 constexpr int kThreads = 512;
 constexpr int kKS = 8;                      // expansion: lanes (column slices) per row
 constexpr int kKW = 8;                      // reduction: column lanes per warp-item
-constexpr int kUPT = 2;                     // update pairs per thread (slab rows x G <= 1024)
+// update pairs (row, right-hand side) per thread: slab rows x G <= kThreads * upt(G)
+__host__ __device__ constexpr int upt(int G) { return G >= 8 ? 1 : 2; }
 constexpr long long kWaitLimit = 1LL << 22; // bounded waits (about a second)
 
 typedef unsigned long long u64;
@@ -59,14 +66,43 @@ __device__ __forceinline__ void upk2(u64 v, float& lo, float& hi) {
 __device__ __forceinline__ void fma2(u64& acc, u64 a, u64 b) {
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
+
+// Tagged partial sums in L2.  Naturally aligned 8-byte accesses are single-copy atomic,
+// so one tag bit (bit 0, the lowest mantissa bit of the real part in complex64, of each
+// part in complex128) per 8-byte word identifies the step that wrote the word.
+template <typename R> struct Tagged;
+template <> struct Tagged<float> {
+  typedef u64 W;     // one complex64 value: (re, im) in one 8-byte word
+  static __device__ __forceinline__ W pack(Cx<float> v, unsigned tag) {
+    return (u64)((__float_as_uint(v.re) & ~1u) | tag) | ((u64)__float_as_uint(v.im) << 32);
+  }
+  static __device__ __forceinline__ bool ok(W w, unsigned tag) { return ((unsigned)w & 1u) == tag; }
+  static __device__ __forceinline__ Cx<float> value(W w) {
+    return Cx<float>(__uint_as_float((unsigned)w), __uint_as_float((unsigned)(w >> 32)));
+  }
+  static __device__ __forceinline__ void store(W* p, W w) { __stcg(reinterpret_cast<unsigned long long*>(p), w); }
+  static __device__ __forceinline__ W load(const W* p) { return __ldcg(reinterpret_cast<const unsigned long long*>(p)); }
+};
+template <> struct Tagged<double> {
+  typedef ulonglong2 W;   // one complex128 value: two 8-byte words, each tagged
+  static __device__ __forceinline__ u64 tag64(double x, unsigned tag) {
+    return ((u64)__double_as_longlong(x) & ~1ull) | (u64)tag;
+  }
+  static __device__ __forceinline__ W pack(Cx<double> v, unsigned tag) {
+    W w;
+    w.x = tag64(v.re, tag);
+    w.y = tag64(v.im, tag);
+    return w;
+  }
+  static __device__ __forceinline__ bool ok(W w, unsigned tag) {
+    return ((unsigned)w.x & 1u) == tag && ((unsigned)w.y & 1u) == tag;
+  }
+  static __device__ __forceinline__ Cx<double> value(W w) {
+    return Cx<double>(__longlong_as_double((long long)w.x), __longlong_as_double((long long)w.y));
+  }
+  static __device__ __forceinline__ void store(W* p, W w) { __stcg(p, w); }
+  static __device__ __forceinline__ W load(const W* p) { return __ldcg(p); }
+};
 
 // complex multiply-accumulate in the storage precision
 template <typename R> struct Mac;
@@ -118,7 +154,7 @@ __device__ __forceinline__ void load_row(const Cx<R>* p, typename Mac<R>::X (&v)
 }
 
 template <typename R>
-struct FlagArgs {
+struct TeamArgs {
   int n, L, leaf, nnodes, dC, C, nteams, nrhs, ngroups, slab_max, nl, rcap;
   long long N, pack_stride;
   unsigned stage_bytes;
@@ -131,11 +167,10 @@ struct FlagArgs {
   const c128* r;
   c128* z;
   Cx<R>* w;
-  Cx<R>* xch;          // ancestors' partial sums: [2][nteams][C][dC][rcap][G]
+  typename Tagged<R>::W* xch;   // ancestors' tagged partial sums: [2][nteams][C][dC][rcap][G]
   int* status;
-  unsigned* flags;     // [nteams * C], zero at launch
   // shared-memory plan (byte offsets)
-  unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_btab, o_x[2],
+  unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_btab, o_etab[2], o_x[2],
       o_qanc, o_qloc, o_mbar, o_flags;
 };
 
@@ -181,10 +216,12 @@ __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const C
 }
 
 template <typename R, int G>
-__global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   using M = Mac<R>;
+  using T = Tagged<R>;
   constexpr int GS = vstride<R>(G);
+  constexpr int kUPT = upt(G);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n, L = a.L, dC = a.dC, nl = a.nl, lf = a.leaf, SM = a.slab_max;
   const int team = blockIdx.x / a.C, c = blockIdx.x % a.C;
@@ -202,12 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
   int* s_ctr = reinterpret_cast<int*>(sm + a.o_flags) + 1;     // reduction item counters [2]
   Cx<R>* qanc = reinterpret_cast<Cx<R>*>(sm + a.o_qanc);
   Cx<R>* qloc = reinterpret_cast<Cx<R>*>(sm + a.o_qloc);
-  // per (slab leaf j, depth d): block offset, row stride, rank, vector block (shared byte offset)
+  // per (slab leaf j, depth d): block offset and row stride (for the row offsets), and,
+  // double-buffered by step parity, rank and vector block (shared byte offset)
   int* boff = reinterpret_cast<int*>(sm + a.o_btab);
   int* brs = boff + nl * L1;
-  int* erk = brs + nl * L1;
-  int* evo = erk + nl * L1;
-  unsigned* tflags = a.flags + (long long)team * a.C;
 
   for (int v = tid; v < a.nnodes; v += kThreads) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
   __syncthreads();
@@ -251,18 +286,14 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
 
   const int nsteps = 2 * n - 1;
   const int ngroups_team = a.ngroups > team ? (a.ngroups - 1 - team) / a.nteams + 1 : 0;
-  const long long total_steps = (long long)ngroups_team * nsteps;
+  const int total_steps = ngroups_team * nsteps;
+  auto layer_of = [&](int s) { return s < n ? s : 2 * n - 2 - s; };
+  auto inc3 = [](int v) { return v == 2 ? 0 : v + 1; };
 
-  auto step_layer = [&](long long t) {
-    const int s = (int)(t % nsteps);
-    return s < n ? s : 2 * n - 2 - s;
-  };
-  // warp 0: cp.async of the ranks of the slab's nodes and the record offsets of step t
-  // (slot t % 3, two steps ahead)
-  auto load_tables = [&](long long t) {
-    if (t >= total_steps) return;
-    const int m = step_layer(t);
-    const int slot3 = (int)(t % 3);
+  // warp 0: cp.async of the ranks of the slab's nodes and the record offsets of the
+  // step at sweep position s into table slot slot3
+  auto load_tables = [&](int s, int slot3) {
+    const int m = layer_of(s);
     int* trk = reinterpret_cast<int*>(sm + a.o_trk[slot3]);
     long long* sro = reinterpret_cast<long long*>(sm + a.o_ro[slot3]);
     const int* rk = a.rank + (long long)m * a.nnodes;
@@ -282,43 +313,49 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
       }
     }
   };
-  // all threads: per (slab leaf, depth) block of step t's record its offset, row stride,
-  // rank and the shared-memory vector block the expansion multiplies it with
-  auto build_btab = [&](long long t) {
-    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
-    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
-    auto rank_at = [&](int lam, int d) {
-      return d <= dC ? trk[d - 1] : trk[dC + (1 << (d - dC)) - 2 + ((lam >> (L - d)) - (vc << (d - dC)))];
-    };
-    for (int e = tid; e < nl * L1; e += kThreads) {
-      const int j = e / L1, d = e % L1;
+  // warp 0 (lane = depth): per (slab leaf, depth) block of the record in table slot
+  // slot3: offset, row stride, rank and the shared-memory vector block the expansion
+  // multiplies it with (into etab buffer eb)
+  auto build_btab = [&](int slot3, int eb) {
+    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[slot3]);
+    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[slot3]);
+    int* erk = reinterpret_cast<int*>(sm + a.o_etab[eb]);
+    int* evo = erk + nl * L1;
+    const int d = lane;
+    for (int j = 0; j < nl; ++j) {
       const int lam = lam0 + j;
       const int sl = s_sz[lam];
-      int o = (int)(sro[j] - sro[0]);
-      if (d > 0) {
-        o += lf * lf;
-        for (int dd = 1; dd < d; ++dd) o += sl * row_stride(rank_at(lam, dd));
-      }
-      boff[e] = o;
-      if (d == 0) {
-        brs[e] = lf;
-        erk[e] = sl;
-        evo[e] = 0;
-      } else {
-        const int r = rank_at(lam, d);
-        brs[e] = row_stride(r);
-        erk[e] = r;
+      int r = 0, vo = 0;
+      if (d >= 1 && d <= L) {
         if (d <= dC) {
-          evo[e] = (int)a.o_qanc + (int)sizeof(Cx<R>) * ((d - 1) * a.rcap * GS);
+          r = trk[d - 1];
+          vo = (int)a.o_qanc + (int)sizeof(Cx<R>) * ((d - 1) * a.rcap * GS);
         } else {
           const int jn = (lam >> (L - d)) - (vc << (d - dC));
-          evo[e] = (int)a.o_qloc + (int)sizeof(Cx<R>) * (dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * GS);
+          r = trk[dC + (1 << (d - dC)) - 2 + jn];
+          vo = (int)a.o_qloc + (int)sizeof(Cx<R>) * (dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * GS);
         }
+      }
+      const int rs = d == 0 ? lf : row_stride(r);
+      // offsets: leaf block first, then the depth blocks in order (exclusive scan)
+      const int term = (d >= 1 && d <= L) ? sl * rs : 0;
+      int incl = term;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      const int base = (int)(sro[j] - sro[0]);
+      if (d <= L) {
+        boff[j * L1 + d] = d == 0 ? base : base + lf * lf + incl - term;
+        brs[j * L1 + d] = rs;
+        erk[j * L1 + d] = d == 0 ? sl : r;
+        evo[j * L1 + d] = vo;
       }
     }
   };
-  // all threads: the per-row offsets of every block of the record of the step whose
-  // block tables were built last
+  // all threads: the per-row offsets of every block of the record whose block tables
+  // were built last
   auto build_rows = [&]() {
     int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff);
     for (int e = tid; e < ns * L1; e += kThreads) {
@@ -328,12 +365,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
       rowoff[d * SM + i] = boff[j * L1 + d] + (lo_c + i - s_lo[lam]) * brs[j * L1 + d];
     }
   };
-  // warp 0, lane 0: the bulk copy of step t's factor record into stage t & 1
-  auto produce = [&](long long t) {
-    if (t >= total_steps || lane != 0) return;
-    const int m = step_layer(t);
-    const int slot = (int)(t & 1);
-    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[t % 3]);
+  // warp 0, lane 0: the bulk copy of the record of sweep position s (tables in slot3)
+  // into stage `slot`
+  auto produce = [&](int s, int slot3, int slot) {
+    if (lane != 0) return;
+    const int m = layer_of(s);
+    const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[slot3]);
     const unsigned bytes = (unsigned)((sro[nl] - sro[0]) * (long long)sizeof(Cx<R>));
     unsigned long long* mb = &mbar[slot];
     if (bytes > a.stage_bytes || bytes == 0) {
@@ -346,30 +383,28 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
     }
   };
 
-  if (warp == 0) {
-    load_tables(0);
-    load_tables(1);
+  if (warp == 0 && total_steps > 0) {
+    load_tables(0, 0);
+    if (total_steps > 1) load_tables(1, 1);
     cp_async_commit();
     cp_async_wait0();
     __syncwarp();
-    produce(0);
+    produce(0, 0, 0);
+    build_btab(0, 0);
   }
-  __syncthreads();
-  if (total_steps > 0) build_btab(0);
   __syncthreads();
   if (total_steps > 0) build_rows();
   __syncthreads();
 
-  long long issued = total_steps > 0 ? 1 : 0;   // bulk copies issued (steps 0 .. issued-1)
-  long long t = 0;
+  int issued = total_steps > 0 ? 1 : 0;   // bulk copies issued (steps 0 .. issued-1)
+  int t = 0, s = 0, grp = team, slot3 = 0;   // slot3 = t % 3
   for (; t < total_steps; ++t) {
-    const int s = (int)(t % nsteps);
-    const int grp = team + (int)(t / nsteps) * a.nteams;
     const int g0 = grp * G;
     const int gcount = (a.nrhs - g0) < G ? (a.nrhs - g0) : G;
     const bool fwd = s < n;
     const int m = fwd ? s : 2 * n - 2 - s;
-    const int slot = (int)(t & 1);
+    const int slot = t & 1;
+    const unsigned tag = (unsigned)(t >> 1) & 1u;
     Cx<R>* x = reinterpret_cast<Cx<R>*>(sm + a.o_x[s & 1]);
     Cx<R>* xn = reinterpret_cast<Cx<R>*>(sm + a.o_x[(s + 1) & 1]);
     // the expansion's result y is held in the next step's x buffer: the update reads
@@ -418,9 +453,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
     }
     const Cx<R>* st = reinterpret_cast<const Cx<R>*>(sm + a.o_stage[slot]);
     const int* rowoff = reinterpret_cast<const int*>(sm + a.o_rowoff);
-    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[t % 3]);
+    const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[slot3]);
     const int* wdesc = reinterpret_cast<const int*>(sm + a.o_wdesc);
-    const int par = (int)(t & 1);
+    const int* erk = reinterpret_cast<const int*>(sm + a.o_etab[slot]);
+    const int* evo = erk + nl * L1;
+    typename T::W* xpart = a.xch + ((long long)slot * a.nteams + team) * a.C * dC * a.rcap * G;
 
     // reduction warp-items [wb, we), taken from the shared counter s_ctr[which]
     auto reduce_items = [&](int wb, int we, int which) {
@@ -445,18 +482,25 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
           rb = s_lo[v] - lo_c;
           re = rb + s_sz[v];
         }
-        if (kc * kKW >= r) continue;           // the whole item is past the rank
+        // every exchanged slot below qcap is rewritten every step (zero past the rank),
+        // so a slot never holds a value older than two steps
         Cx<R> out[G];
-        reduce_col<R, G, GS>(st, rowoff + d * SM, x, rb, re, rl, min(k, r - 1), out);
+        if (kc * kKW < r) {
+          reduce_col<R, G, GS>(st, rowoff + d * SM, x, rb, re, rl, min(k, r - 1), out);
 #pragma unroll
-        for (int g = 0; g < G; ++g)
+          for (int g = 0; g < G; ++g)
 #pragma unroll
-          for (int o = kKW; o < 32; o <<= 1) out[g] += shfl_xor(out[g], o);
-        if (rl == 0 && k < r && k < qcap) {
+            for (int o = kKW; o < 32; o <<= 1) out[g] += shfl_xor(out[g], o);
+        } else {
+          if (d > dC) continue;           // a subtree item wholly past the rank
+#pragma unroll
+          for (int g = 0; g < G; ++g) out[g] = Cx<R>(0, 0);
+        }
+        if (rl == 0 && k < qcap && (k < r || d <= dC)) {
           if (d <= dC) {
-            Cx<R>* dst = a.xch + ((((long long)par * a.nteams + team) * a.C + c) * dC + (d - 1)) * a.rcap * G + k * G;
+            typename T::W* dst = xpart + ((long long)c * dC + (d - 1)) * a.rcap * G + k * G;
 #pragma unroll
-            for (int g = 0; g < G; ++g) st_cg(dst + g, out[g]);
+            for (int g = 0; g < G; ++g) T::store(dst + g, T::pack(k < r ? out[g] : Cx<R>(0, 0), tag));
           } else {
             Cx<R>* dst = qloc + dt[DT_QBASE + d] + (jn * qcap + k) * GS;
 #pragma unroll
@@ -466,88 +510,78 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
       }
     };
 
-    // ---- 1. warp 0 issues step t + 1's bulk copy and step t + 2's tables; then all
-    //         warps compute the ancestors' partial sums --------------------------------
+    // ---- 0.-3. warp 0: next bulk copy and tables; all warps: ancestor partial sums,
+    //            subtree reductions, then the gather of the sibling subtrees' sums ----
     const bool ok1 = *s_fail == 0;
-    if (warp == 0) {
+    if (warp == 0 && ok1 && t + 1 < total_steps) {
+      const int s1 = s + 1 == nsteps ? 0 : s + 1;
       cp_async_wait0();      // the tables of step t + 1
       __syncwarp();
-      if (ok1) {
-        produce(t + 1);
-        load_tables(t + 2);
+      produce(s1, inc3(slot3), slot ^ 1);
+      if (t + 2 < total_steps) {
+        load_tables(s1 + 1 == nsteps ? 0 : s1 + 1, inc3(inc3(slot3)));
         cp_async_commit();
       }
+      build_btab(inc3(slot3), slot ^ 1);
+      issued = t + 2;
     }
-    if (ok1) reduce_items(0, dt[DT_WSTART + dC + 1], 0);
-    if (ok1 && t + 1 < total_steps) issued = t + 2;
-    __syncthreads();
-
-    // ---- 2. publish; subtree reductions while warp 0 waits for the team ---------------
-    if (warp == 0) {
-      if (tid == 0) {
-        __threadfence();
-        st_release(tflags + c, (unsigned)(t + 1));
-      }
-      for (int cc = lane; cc < a.C; cc += 32) {
-        if (cc == c) continue;
-        long long spins = 0;
-        while (ld_acquire(tflags + cc) < (unsigned)(t + 1)) {
-          if (*(volatile int*)a.status != 0) { *s_fail = 1; break; }
-          if (++spins > kWaitLimit) {
-            report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
-            *s_fail = 1;
-            break;
-          }
-        }
-      }
-      __threadfence();
-      __syncwarp();
-    } else if (*s_fail == 0) {
+    if (ok1) {
+      reduce_items(0, dt[DT_WSTART + dC + 1], 0);
       reduce_items(dt[DT_WSTART + dC + 1], dt[DT_WSTART + L + 1], 1);
-    }
-    __syncthreads();
-    if (*s_fail != 0) break;
-
-    // ---- 3. sums over the sibling subtree of every ancestor (all loads of a thread's
-    //         items in flight together); the next step's block tables ------------------
-    {
       constexpr int GJ = sizeof(R) == 4 ? 3 : 1;
       const int rg = a.rcap * G;
       const int tot = dC * rg;
       const long long cstride = (long long)dC * rg;
-      const Cx<R>* xb = a.xch + ((long long)par * a.nteams + team) * a.C * cstride;
+      const typename T::W* xb = a.xch + ((long long)slot * a.nteams + team) * a.C * cstride;
       for (int base = tid; base < tot; base += GJ * kThreads) {
-        Cx<R> vals[GJ][8];
+        typename T::W vals[GJ][8];
+        const typename T::W* src[GJ];
+        int span[GJ];
+        bool use[GJ];
 #pragma unroll
         for (int j = 0; j < GJ; ++j) {
           const int it = base + j * kThreads;
           const int d = it < tot ? it / rg + 1 : 1;
           const int kg = it - (d - 1) * rg;
-          const int span = 1 << (dC - d);
+          span[j] = 1 << (dC - d);
           const int c0 = (((vc >> (dC - d)) ^ 1) << (dC - d)) - (1 << dC);
-          const bool use = it < tot && kg / G < trk[d - 1];
-          const Cx<R>* src = xb + (long long)(d - 1) * rg + kg + (long long)c0 * cstride;
+          use[j] = it < tot && kg / G < trk[d - 1];
+          src[j] = xb + (long long)(d - 1) * rg + kg + (long long)c0 * cstride;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) vals[j][u] = (use && u < span) ? ld_cg(src + u * cstride) : Cx<R>(0, 0);
-          if (use) {
-            for (int cc = 8; cc < span; ++cc) vals[j][0] += ld_cg(src + cc * cstride);   // teams over 16 CTAs
-          }
+          for (int u = 0; u < 8; ++u)
+            if (use[j] && u < span[j]) vals[j][u] = T::load(src[j] + u * cstride);
         }
 #pragma unroll
         for (int j = 0; j < GJ; ++j) {
           const int it = base + j * kThreads;
-          if (it < tot) {
-            Cx<R> acc = vals[j][0];
+          if (it >= tot) continue;
+          Cx<R> acc(0, 0);
+          if (use[j]) {
+            auto settle = [&](typename T::W v, int u) {   // re-read until written for this step
+              long long spins = 0;
+              while (!T::ok(v, tag)) {
+                if (++spins > kWaitLimit || *(volatile int*)a.status != 0) {
+                  report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
+                  *s_fail = 1;
+                  break;
+                }
+                v = T::load(src[j] + u * cstride);
+              }
+              acc += T::value(v);
+            };
 #pragma unroll
-            for (int u = 1; u < 8; ++u) acc += vals[j][u];
-            const int d = it / rg + 1;
-            const int kg = it - (d - 1) * rg;
-            qanc[(d - 1) * a.rcap * GS + (kg / G) * GS + kg % G] = acc;
+            for (int u = 0; u < 8; ++u)
+              if (u < span[j]) settle(vals[j][u], u);
+            for (int u = 8; u < span[j]; ++u) settle(T::load(src[j] + u * cstride), u);
           }
+          const int d = it / rg + 1;
+          const int kg = it - (d - 1) * rg;
+          qanc[(d - 1) * a.rcap * GS + (kg / G) * GS + kg % G] = acc;
         }
       }
     }
     __syncthreads();
+    if (*s_fail != 0) break;
 
     // ---- 4. expansion: lane = (row i, column slice ks) --------------------------------
     {
@@ -585,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
     __syncthreads();
 
     // ---- 5. the update of Algorithm 2.6 for this thread's (row, rhs) pairs; the next
-    //         step's block tables ---------------------------------------------------------
+    //         step's row offsets ---------------------------------------------------------
 #pragma unroll
     for (int u = 0; u < kUPT; ++u) {
       const int p = tid + u * kThreads;
@@ -610,15 +644,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
         }
       }
     }
-    if (t + 1 < total_steps) build_btab(t + 1);
+    if (t + 1 < total_steps) build_rows();
     if (tid == 0) { s_ctr[0] = 0; s_ctr[1] = 0; }
     __syncthreads();
-    if (t + 1 < total_steps) build_rows();
-    __syncthreads();
+    if (++s == nsteps) { s = 0; grp += a.nteams; }
+    slot3 = inc3(slot3);
   }
   // a CTA that stopped early still owns the bulk copies it issued: wait for them
   if (tid == 0) {
-    for (long long q = t + 1; q < issued; ++q) {
+    for (int q = t + 1; q < issued; ++q) {
       long long spins = 0;
       const unsigned parity = (unsigned)((q >> 1) & 1);
       while (!mbar_try_wait(&mbar[q & 1], parity) && ++spins <= kWaitLimit) {
@@ -632,24 +666,24 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_flag_kernel(FlagArgs<R> a) 
 
 namespace {
 
-struct FlagConfig {
+struct TeamConfig {
   bool ok;
   int dC, C, G, nteams;
   size_t smem;
 };
 
-static int ilog2f(int x) { int l = 0; while ((1 << (l + 1)) <= x) ++l; return l; }
+static int ilog2t(int x) { int l = 0; while ((1 << (l + 1)) <= x) ++l; return l; }
 
 // shared-memory plan for (dC, G); returns total bytes (0 if the layout is not supported)
 template <typename R>
-static size_t plan_flag(const hsweep_s* h, int dC, int G, FlagArgs<R>& a) {
+static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a) {
   const size_t es = sizeof(Cx<R>);
   const int L = h->L;
   const int nl = 1 << (L - dC);
   const int slab_max = h->tree.maxsz(dC);
   const int rcap = std::max(1, h->rank_max);
   const int GS = vstride<R>(G);
-  if (L > 14 || (long long)slab_max * G > (long long)kUPT * kThreads || h->leaf > 8) return 0;
+  if (L > 14 || (long long)slab_max * G > (long long)upt(G) * kThreads || h->leaf > 8) return 0;
   auto al = [](size_t x, size_t b) { return (x + b - 1) / b * b; };
   size_t o = 0;
   const size_t stage = al((size_t)h->slab_bytes_max[dC], 128);
@@ -670,7 +704,8 @@ static size_t plan_flag(const hsweep_s* h, int dC, int G, FlagArgs<R>& a) {
     if (d > dC) qloc += (long long)nodes * qcap * GS;
   }
   a.o_wdesc = (unsigned)o; o += al((size_t)wtot * sizeof(int), 16);
-  a.o_btab = (unsigned)o; o += al((size_t)4 * nl * (L + 1) * sizeof(int), 16);
+  a.o_btab = (unsigned)o; o += al((size_t)2 * nl * (L + 1) * sizeof(int), 16);
+  for (int b = 0; b < 2; ++b) { a.o_etab[b] = (unsigned)o; o += al((size_t)2 * nl * (L + 1) * sizeof(int), 16); }
   for (int b = 0; b < 2; ++b) { a.o_x[b] = (unsigned)o; o += al((size_t)slab_max * GS * es, 16); }
   a.o_qanc = (unsigned)o; o += al((size_t)std::max(1, dC) * rcap * GS * es, 16);
   a.o_qloc = (unsigned)o; o += al((size_t)std::max(1LL, qloc) * es, 16);
@@ -685,7 +720,7 @@ static size_t plan_flag(const hsweep_s* h, int dC, int G, FlagArgs<R>& a) {
 
 template <typename R, int G>
 static int resident_ctas(const hsweep_s* h, size_t smem) {
-  auto kern = sweep_flag_kernel<R, G>;
+  auto kern = sweep_team_kernel<R, G>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -710,22 +745,22 @@ static int resident_for(const hsweep_s* h, int G, size_t smem) {
 }
 
 // Team size C and right-hand sides per team G: the fewest rounds of 2n-1 dependent
-// steps, a step costing a fixed latency (flag exchange, barriers) plus work that grows
+// steps, a step costing a fixed latency (exchange through L2, barriers) plus work that grows
 // with the slab's rows times G.
 template <typename R>
-static FlagConfig choose_flag(const hsweep_s* h, int nrhs) {
-  FlagConfig best{};
+static TeamConfig choose_team(const hsweep_s* h, int nrhs) {
+  TeamConfig best{};
   best.ok = false;
   double best_cost = 1e300;
   const size_t cap = 227 * 1024;
   const int C_pref = h->opt.team, G_pref = h->opt.groups;
   for (int C = 1; C <= h->nleaves && C <= h->num_sms; C *= 2) {
-    if (C_pref > 0 && C != (1 << ilog2f(C_pref))) continue;
-    const int dC = ilog2f(C);
+    if (C_pref > 0 && C != (1 << ilog2t(C_pref))) continue;
+    const int dC = ilog2t(C);
     for (int G : {8, 5, 4, 2, 1}) {
       if (G_pref > 0 && G != G_pref) continue;
-      FlagArgs<R> a;
-      const size_t smem = plan_flag<R>(h, dC, G, a);
+      TeamArgs<R> a;
+      const size_t smem = plan_team<R>(h, dC, G, a);
       if (smem == 0 || smem > cap) continue;
       const int resident = resident_for<R>(h, G, smem);
       const int teams_cap = std::min(resident, 1024) / C;
@@ -738,7 +773,7 @@ static FlagConfig choose_flag(const hsweep_s* h, int nrhs) {
       const double cost = rounds * step;
       if (cost < best_cost - 1e-9) {
         best_cost = cost;
-        best = FlagConfig{true, dC, C, G, teams, smem};
+        best = TeamConfig{true, dC, C, G, teams, smem};
       }
     }
   }
@@ -746,8 +781,8 @@ static FlagConfig choose_flag(const hsweep_s* h, int nrhs) {
 }
 
 template <typename R, int G>
-static int launch_flag(hsweep_s* h, const FlagConfig& cfg, FlagArgs<R>& a) {
-  auto kern = sweep_flag_kernel<R, G>;
+static int launch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
+  auto kern = sweep_team_kernel<R, G>;
   HSW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
@@ -777,20 +812,20 @@ static int launch_flag(hsweep_s* h, const FlagConfig& cfg, FlagArgs<R>& a) {
 }
 
 template <typename R>
-static int dispatch_flag(hsweep_s* h, const FlagConfig& cfg, FlagArgs<R>& a) {
+static int dispatch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
   switch (cfg.G) {
-    case 1: return launch_flag<R, 1>(h, cfg, a);
-    case 2: return launch_flag<R, 2>(h, cfg, a);
-    case 4: return launch_flag<R, 4>(h, cfg, a);
-    case 5: return launch_flag<R, 5>(h, cfg, a);
-    default: return launch_flag<R, 8>(h, cfg, a);
+    case 1: return launch_team<R, 1>(h, cfg, a);
+    case 2: return launch_team<R, 2>(h, cfg, a);
+    case 4: return launch_team<R, 4>(h, cfg, a);
+    case 5: return launch_team<R, 5>(h, cfg, a);
+    default: return launch_team<R, 8>(h, cfg, a);
   }
 }
 
-static long long al256f(long long x) { return (x + 255) / 256 * 256; }
+static long long al256t(long long x) { return (x + 255) / 256 * 256; }
 
 template <typename R>
-static void flag_scratch_need(const hsweep_s* h, int nrhs, const FlagConfig& cfg, long long* w_bytes,
+static void team_scratch_need(const hsweep_s* h, int nrhs, const TeamConfig& cfg, long long* w_bytes,
                               long long* x_bytes) {
   const long long es = sizeof(Cx<R>);
   *w_bytes = (long long)nrhs * h->N * es;
@@ -798,20 +833,20 @@ static void flag_scratch_need(const hsweep_s* h, int nrhs, const FlagConfig& cfg
 }
 
 template <typename R>
-static int apply_flag_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch,
+static int apply_team_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch,
                            size_t scratch_bytes) {
   *used = false;
-  FlagConfig cfg = choose_flag<R>(h, nrhs);
+  TeamConfig cfg = choose_team<R>(h, nrhs);
   if (!cfg.ok) return HSWEEP_OK;
   const size_t es = sizeof(Cx<R>);
   long long wb, xb;
-  flag_scratch_need<R>(h, nrhs, cfg, &wb, &xb);
+  team_scratch_need<R>(h, nrhs, cfg, &wb, &xb);
   void* wptr;
   void* xptr;
   if (scratch) {    // caller-provided scratch: nothing is allocated
-    if ((size_t)(al256f(wb) + al256f(xb)) > scratch_bytes) return HSWEEP_ERR_ARG;
+    if ((size_t)(al256t(wb) + al256t(xb)) > scratch_bytes) return HSWEEP_ERR_ARG;
     wptr = scratch;
-    xptr = (unsigned char*)scratch + al256f(wb);
+    xptr = (unsigned char*)scratch + al256t(wb);
   } else {
     const long long need_w = (long long)nrhs * h->N;
     if (need_w > h->wcache_cap) {
@@ -830,8 +865,8 @@ static int apply_flag_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
     wptr = h->d_wcache;
     xptr = h->d_xch;
   }
-  FlagArgs<R> a;
-  plan_flag<R>(h, cfg.dC, cfg.G, a);
+  TeamArgs<R> a;
+  plan_team<R>(h, cfg.dC, cfg.G, a);
   a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.nnodes = h->nnodes; a.dC = cfg.dC; a.C = cfg.C;
   a.nteams = cfg.nteams; a.nrhs = nrhs; a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
   a.N = h->N; a.pack_stride = h->pack_stride;
@@ -839,52 +874,53 @@ static int apply_flag_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
   a.pack = reinterpret_cast<const Cx<R>*>(h->d_pack);
   a.north = h->d_north; a.r = r; a.z = z;
   a.w = reinterpret_cast<Cx<R>*>(wptr);
-  a.xch = reinterpret_cast<Cx<R>*>(xptr);
-  a.status = h->d_status; a.flags = h->d_flags;
+  a.xch = reinterpret_cast<typename Tagged<R>::W*>(xptr);
+  a.status = h->d_status;
   const bool prof = h->prof;
   if (scratch) h->prof = false;   // the no-allocation path creates no events
   int rc = HSWEEP_OK;
-  if (cudaMemsetAsync(h->d_flags, 0, (size_t)cfg.nteams * cfg.C * sizeof(unsigned), h->stream) != cudaSuccess)
+  // every exchange slot starts with the tag bit set: steps 0 and 1 expect it clear
+  if (cudaMemsetAsync(xptr, 0xff, (size_t)xb, h->stream) != cudaSuccess)
     rc = HSWEEP_ERR_CUDA;
-  if (rc == HSWEEP_OK) rc = dispatch_flag<R>(h, cfg, a);
+  if (rc == HSWEEP_OK) rc = dispatch_team<R>(h, cfg, a);
   h->prof = prof;
   if (rc == HSWEEP_OK) *used = true;
   return rc;
 }
 
-static bool flag_usable(const hsweep_s* h) {
-  return h->pack_valid && !h->slab_bytes_max.empty() && h->d_flags != nullptr;
+static bool team_usable(const hsweep_s* h) {
+  return h->pack_valid && !h->slab_bytes_max.empty();
 }
 
 }  // namespace
 
-int hsw_flag_plan(hsweep_s* h, int nrhs, long long* out) {
-  FlagConfig cfg{};
-  if (flag_usable(h)) cfg = h->prec == HSWEEP_FP64 ? choose_flag<double>(h, nrhs) : choose_flag<float>(h, nrhs);
+int hsw_team_plan(hsweep_s* h, int nrhs, long long* out) {
+  TeamConfig cfg{};
+  if (team_usable(h)) cfg = h->prec == HSWEEP_FP64 ? choose_team<double>(h, nrhs) : choose_team<float>(h, nrhs);
   if (!cfg.ok) return 0;
   out[0] = 2; out[1] = cfg.C; out[2] = cfg.G; out[3] = cfg.nteams; out[4] = 0;
   out[5] = (long long)cfg.smem; out[6] = h->slab_bytes_max[cfg.dC]; out[7] = kKS;
   return 1;
 }
 
-int hsw_apply_flag(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch, size_t scratch_bytes) {
+int hsw_apply_team(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch, size_t scratch_bytes) {
   *used = false;
-  if (!flag_usable(h)) return HSWEEP_OK;
-  if (h->prec == HSWEEP_FP64) return apply_flag_impl<double>(h, r, z, nrhs, used, scratch, scratch_bytes);
-  return apply_flag_impl<float>(h, r, z, nrhs, used, scratch, scratch_bytes);
+  if (!team_usable(h)) return HSWEEP_OK;
+  if (h->prec == HSWEEP_FP64) return apply_team_impl<double>(h, r, z, nrhs, used, scratch, scratch_bytes);
+  return apply_team_impl<float>(h, r, z, nrhs, used, scratch, scratch_bytes);
 }
 
-size_t hsw_apply_flag_scratch_bytes(hsweep_s* h, int nrhs) {
-  if (!flag_usable(h)) return 0;
+size_t hsw_apply_team_scratch_bytes(hsweep_s* h, int nrhs) {
+  if (!team_usable(h)) return 0;
   long long wb, xb;
   if (h->prec == HSWEEP_FP64) {
-    FlagConfig cfg = choose_flag<double>(h, nrhs);
+    TeamConfig cfg = choose_team<double>(h, nrhs);
     if (!cfg.ok) return 0;
-    flag_scratch_need<double>(h, nrhs, cfg, &wb, &xb);
+    team_scratch_need<double>(h, nrhs, cfg, &wb, &xb);
   } else {
-    FlagConfig cfg = choose_flag<float>(h, nrhs);
+    TeamConfig cfg = choose_team<float>(h, nrhs);
     if (!cfg.ok) return 0;
-    flag_scratch_need<float>(h, nrhs, cfg, &wb, &xb);
+    team_scratch_need<float>(h, nrhs, cfg, &wb, &xb);
   }
-  return (size_t)(al256f(wb) + al256f(xb));
+  return (size_t)(al256t(wb) + al256t(xb));
 }

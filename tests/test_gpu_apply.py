@@ -103,7 +103,7 @@ def test_apply_full_rank_blocks_and_repeat_calls_agree(hs):
 @pytest.mark.parametrize("n,prec,nrhs,team", [(127, 0, 1, 0), (127, 1, 9, 0), (255, 0, 2, 32), (255, 1, 64, 0),
                                               (64, 1, 3, 4), (37, 0, 2, 0), (255, 1, 17, 0), (255, 0, 5, 0)])
 def test_tma_sweeps_match_basic_sweep_and_exact(hs, n, prec, nrhs, team, kernel):
-    # kernel 0: the automatic choice (the flag-synchronised kernel where it fits);
+    # kernel 0: the automatic choice (the cooperative-team kernel where it fits);
     # kernel 2: the thread-block-cluster kernel
     c, omega, pml = _problem(n, 4)
     disc = Discretization(c, omega, pml)
