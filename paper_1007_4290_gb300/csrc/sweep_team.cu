@@ -8,7 +8,7 @@
 // Algorithm 2.6) runs as:
 //   0. the layer's factor record for the slab (leaf-major packed layout, pack.cu) is
 //      already in shared memory: warp 0 issued its bulk copy one step ahead (mbarrier),
-//      and now issues the next one and builds the next step's block tables;
+//      and now issues the next one;
 //   1. partial sums q_v = F_v^t x over the slab's rows for the ancestors v at depths
 //      1..dC (their rows span several CTAs), stored to L2 with a step tag;
 //   2. the reductions of the CTA's own subtree (depths > dC), then
@@ -18,7 +18,7 @@
 //      every eighth column, all G right-hand sides in registers;
 //   5. the update of Algorithm 2.6 for (row, right-hand side) pairs, one per thread,
 //      with coalesced global reads (prefetched at the start of the step) and writes;
-//      the per-row offsets of the next step's record.
+//      the row offsets and block tables of the next step's record.
 // Three block barriers per step; no team-wide barrier: a CTA waits only for the
 // partial sums it reads.  The tag is the lowest bit of every 8-byte word of a partial
 // sum, equal to bit 1 of the step index: a slot (one per step parity) holds either
@@ -170,7 +170,7 @@ struct TeamArgs {
   typename Tagged<R>::W* xch;   // ancestors' tagged partial sums: [2][nteams][C][dC][rcap][G]
   int* status;
   // shared-memory plan (byte offsets)
-  unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_btab, o_etab[2], o_x[2],
+  unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_etab[2], o_x[2],
       o_qanc, o_qloc, o_mbar, o_flags;
 };
 
@@ -239,10 +239,6 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
   int* s_ctr = reinterpret_cast<int*>(sm + a.o_flags) + 1;     // reduction item counters [2]
   Cx<R>* qanc = reinterpret_cast<Cx<R>*>(sm + a.o_qanc);
   Cx<R>* qloc = reinterpret_cast<Cx<R>*>(sm + a.o_qloc);
-  // per (slab leaf j, depth d): block offset and row stride (for the row offsets), and,
-  // double-buffered by step parity, rank and vector block (shared byte offset)
-  int* boff = reinterpret_cast<int*>(sm + a.o_btab);
-  int* brs = boff + nl * L1;
 
   for (int v = tid; v < a.nnodes; v += kThreads) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
   __syncthreads();
@@ -313,56 +309,51 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
       }
     }
   };
-  // warp 0 (lane = depth): per (slab leaf, depth) block of the record in table slot
-  // slot3: offset, row stride, rank and the shared-memory vector block the expansion
-  // multiplies it with (into etab buffer eb)
-  auto build_btab = [&](int slot3, int eb) {
+  // all threads: from the ranks and record offsets in table slot slot3, the offset of
+  // every row of every block of that step's record (rowoff), and per (slab leaf, depth)
+  // the rank and the shared-memory vector block the expansion multiplies it with (etab
+  // buffer eb)
+  auto build_tables = [&](int slot3, int eb) {
     const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[slot3]);
     const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[slot3]);
+    int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff);
     int* erk = reinterpret_cast<int*>(sm + a.o_etab[eb]);
     int* evo = erk + nl * L1;
-    const int d = lane;
-    for (int j = 0; j < nl; ++j) {
-      const int lam = lam0 + j;
-      const int sl = s_sz[lam];
-      int r = 0, vo = 0;
-      if (d >= 1 && d <= L) {
-        if (d <= dC) {
-          r = trk[d - 1];
-          vo = (int)a.o_qanc + (int)sizeof(Cx<R>) * ((d - 1) * a.rcap * GS);
-        } else {
-          const int jn = (lam >> (L - d)) - (vc << (d - dC));
-          r = trk[dC + (1 << (d - dC)) - 2 + jn];
-          vo = (int)a.o_qloc + (int)sizeof(Cx<R>) * (dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * GS);
-        }
-      }
-      const int rs = d == 0 ? lf : row_stride(r);
-      // offsets: leaf block first, then the depth blocks in order (exclusive scan)
-      const int term = (d >= 1 && d <= L) ? sl * rs : 0;
-      int incl = term;
-#pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-      }
-      const int base = (int)(sro[j] - sro[0]);
-      if (d <= L) {
-        boff[j * L1 + d] = d == 0 ? base : base + lf * lf + incl - term;
-        brs[j * L1 + d] = rs;
-        erk[j * L1 + d] = d == 0 ? sl : r;
-        evo[j * L1 + d] = vo;
-      }
-    }
-  };
-  // all threads: the per-row offsets of every block of the record whose block tables
-  // were built last
-  auto build_rows = [&]() {
-    int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff);
+    auto rank_at = [&](int lam, int d) {
+      return d <= dC ? trk[d - 1] : trk[dC + (1 << (d - dC)) - 2 + ((lam >> (L - d)) - (vc << (d - dC)))];
+    };
     for (int e = tid; e < ns * L1; e += kThreads) {
       const int i = e % ns, d = e / ns;
       const int lam = s_leafnode[i];
       const int j = lam - lam0;
-      rowoff[d * SM + i] = boff[j * L1 + d] + (lo_c + i - s_lo[lam]) * brs[j * L1 + d];
+      const int sl = s_sz[lam], ai = lo_c + i - s_lo[lam];
+      int o = (int)(sro[j] - sro[0]);
+      if (d == 0) {
+        o += ai * lf;
+      } else {
+        o += lf * lf;
+        for (int dd = 1; dd < d; ++dd) o += sl * row_stride(rank_at(lam, dd));
+        o += ai * row_stride(rank_at(lam, d));
+      }
+      rowoff[d * SM + i] = o;
+    }
+    for (int e = tid; e < nl * L1; e += kThreads) {
+      const int j = e / L1, d = e % L1;
+      const int lam = lam0 + j;
+      int r, vo = 0;
+      if (d == 0) {
+        r = s_sz[lam];
+      } else {
+        r = rank_at(lam, d);
+        if (d <= dC) {
+          vo = (int)a.o_qanc + (int)sizeof(Cx<R>) * ((d - 1) * a.rcap * GS);
+        } else {
+          const int jn = (lam >> (L - d)) - (vc << (d - dC));
+          vo = (int)a.o_qloc + (int)sizeof(Cx<R>) * (dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * GS);
+        }
+      }
+      erk[e] = r;
+      evo[e] = vo;
     }
   };
   // warp 0, lane 0: the bulk copy of the record of sweep position s (tables in slot3)
@@ -390,10 +381,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     cp_async_wait0();
     __syncwarp();
     produce(0, 0, 0);
-    build_btab(0, 0);
   }
   __syncthreads();
-  if (total_steps > 0) build_rows();
+  if (total_steps > 0) build_tables(0, 0);
   __syncthreads();
 
   int issued = total_steps > 0 ? 1 : 0;   // bulk copies issued (steps 0 .. issued-1)
@@ -522,7 +512,6 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
         load_tables(s1 + 1 == nsteps ? 0 : s1 + 1, inc3(inc3(slot3)));
         cp_async_commit();
       }
-      build_btab(inc3(slot3), slot ^ 1);
       issued = t + 2;
     }
     if (ok1) {
@@ -644,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
         }
       }
     }
-    if (t + 1 < total_steps) build_rows();
+    if (t + 1 < total_steps) build_tables(inc3(slot3), slot ^ 1);
     if (tid == 0) { s_ctr[0] = 0; s_ctr[1] = 0; }
     __syncthreads();
     if (++s == nsteps) { s = 0; grp += a.nteams; }
@@ -704,7 +693,6 @@ static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a) {
     if (d > dC) qloc += (long long)nodes * qcap * GS;
   }
   a.o_wdesc = (unsigned)o; o += al((size_t)wtot * sizeof(int), 16);
-  a.o_btab = (unsigned)o; o += al((size_t)2 * nl * (L + 1) * sizeof(int), 16);
   for (int b = 0; b < 2; ++b) { a.o_etab[b] = (unsigned)o; o += al((size_t)2 * nl * (L + 1) * sizeof(int), 16); }
   for (int b = 0; b < 2; ++b) { a.o_x[b] = (unsigned)o; o += al((size_t)slab_max * GS * es, 16); }
   a.o_qanc = (unsigned)o; o += al((size_t)std::max(1, dC) * rcap * GS * es, 16);
