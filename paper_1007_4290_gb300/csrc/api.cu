@@ -50,6 +50,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->team = 0;
   o->groups = 0;
   o->sweep_kernel = 0;
+  o->sweep_tc = 0;
   return HSWEEP_OK;
 }
 
@@ -83,7 +84,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       !(eps_H >= 0) || opt.leaf < 2 || opt.leaf > 8 || opt.r_max < 1 || opt.r_max > 56 ||
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
-      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2)
+      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
+      (opt.sweep_tc != 0 && opt.sweep_tc != 1))
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;

@@ -153,9 +153,50 @@ __device__ __forceinline__ void load_row(const Cx<R>* p, typename Mac<R>::X (&v)
   }
 }
 
+// ---- tensor cores: mma.sync m16n8k8 with TF32 operands in three parts ---------------
+// x = hi + lo: hi is x rounded to the 10 explicit mantissa bits of TF32 (integer add
+// and mask, full-rate ALU), lo = x - hi is exact in FP32 and the tensor core reads its
+// top TF32 bits; a product is hi*hi + hi*lo + lo*hi in FP32 accumulation (the dropped
+// lo*lo term and the truncation of lo are below 2^-21 relative).
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// A complex product sum C = sum_k V[k] F[k] over complex k as one real m16n8k8 step:
+// A rows 0..7 give the real parts of eight outputs, rows 8..15 the imaginary parts,
+// real column 2k + p holds part p of complex index k:
+//   A[g][2k] = Re V_g[k], A[g][2k+1] = -Im V_g[k], A[g+8][2k] = Im V_g[k], A[g+8][2k+1] = Re V_g[k]
+//   B[2k + p][n] = part p of F_n[k].
+// Lane (g = lane / 4, t = lane % 4) holds V_g at complex indices k0 + t/2 (va) and
+// k0 + 2 + t/2 (vb); p = t % 2.
+struct TcA {
+  unsigned h[4], l[4];
+  __device__ __forceinline__ void build(Cx<float> va, Cx<float> vb, int p) {
+    split_tf32(p ? -va.im : va.re, h[0], l[0]);
+    split_tf32(p ? va.re : va.im, h[1], l[1]);
+    split_tf32(p ? -vb.im : vb.re, h[2], l[2]);
+    split_tf32(p ? vb.re : vb.im, h[3], l[3]);
+  }
+};
+__device__ __forceinline__ void tc_step(float (&c)[4], float (&c2)[4], const TcA& A, float fa, float fb) {
+  unsigned bh0, bl0, bh1, bl1;
+  split_tf32(fa, bh0, bl0);
+  split_tf32(fb, bh1, bl1);
+  mma_tf32(c, A.h[0], A.h[1], A.h[2], A.h[3], bh0, bh1);
+  mma_tf32(c2, A.l[0], A.l[1], A.l[2], A.l[3], bh0, bh1);
+  mma_tf32(c2, A.h[0], A.h[1], A.h[2], A.h[3], bl0, bl1);
+}
+
 template <typename R>
 struct TeamArgs {
   int n, L, leaf, nnodes, dC, C, nteams, nrhs, ngroups, slab_max, nl, rcap;
+  int tc;              // ancestor contractions on tensor cores (complex64, slab <= 64 rows)
   long long N, pack_stride;
   unsigned stage_bytes;
   const int* lo;
@@ -199,14 +240,14 @@ __device__ __forceinline__ void reduce_col(const Cx<R>* __restrict__ st, const i
   for (int g = 0; g < G; ++g) out[g] = M::get(acc[g]);
 }
 
-// Expansion of one row against one vector block: columns k = kbeg, kbeg + kKS, ...
+// Expansion of one row against one vector block: columns k = kbeg, kbeg + KSTEP, ...
 // < kend of the row F, vectors V[k * GS + g].
-template <typename R, int G, int GS>
+template <typename R, int G, int GS, int KSTEP = kKS>
 __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const Cx<R>* __restrict__ F,
                                            const Cx<R>* __restrict__ V, int kbeg, int kend) {
   using M = Mac<R>;
 #pragma unroll 2
-  for (int k = kbeg; k < kend; k += kKS) {
+  for (int k = kbeg; k < kend; k += KSTEP) {
     const typename M::F f = M::f(F + k);
     typename M::X v[G];
     load_row<R, G>(V + k * GS, v);
@@ -222,6 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
   using T = Tagged<R>;
   constexpr int GS = vstride<R>(G);
   constexpr int kUPT = upt(G);
+  constexpr bool kTC = std::is_same<R, float>::value;
+  const bool tc = kTC && a.tc != 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n, L = a.L, dC = a.dC, nl = a.nl, lf = a.leaf, SM = a.slab_max;
   const int team = blockIdx.x / a.C, c = blockIdx.x % a.C;
@@ -514,8 +557,58 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
       }
       issued = t + 2;
     }
+    // ancestors' partial sums on tensor cores: warp-items (depth d, 16 columns), the
+    // columns as two n-tiles, the slab's rows as the k dimension
+    auto reduce_anc_tc = [&]() {
+      if constexpr (kTC) {
+        const int g = lane >> 2, tq = lane & 3, pp = tq & 1;
+        const int nct = (a.rcap + 15) / 16;
+        for (;;) {
+          int wi = 0;
+          if (lane == 0) wi = atomicAdd(&s_ctr[0], 1);
+          wi = __shfl_sync(0xffffffffu, wi, 0);
+          if (wi >= dC * nct) break;
+          const int d = wi / nct + 1, k0 = (wi % nct) * 16;
+          const int r = trk[d - 1];
+          float cc[2][4] = {}, c2[2][4] = {};
+          if (k0 < r) {
+            const int* ro_d = rowoff + d * SM;
+            for (int i0 = 0; i0 < ns; i0 += 4) {
+              const int ia = i0 + (tq >> 1), ib = ia + 2;
+              const Cx<float> va = (ia < ns && g < G) ? x[ia * GS + g] : Cx<float>(0.f, 0.f);
+              const Cx<float> vb = (ib < ns && g < G) ? x[ib * GS + g] : Cx<float>(0.f, 0.f);
+              TcA A;
+              A.build(va, vb, pp);
+              const float* Fa = reinterpret_cast<const float*>(st + (ia < ns ? ro_d[ia] : 0)) + pp;
+              const float* Fb = reinterpret_cast<const float*>(st + (ib < ns ? ro_d[ib] : 0)) + pp;
+#pragma unroll
+              for (int nt = 0; nt < 2; ++nt) {
+                const int kk = k0 + 8 * nt + g;
+                const float fa = (ia < ns && kk < r) ? Fa[2 * kk] : 0.f;
+                const float fb = (ib < ns && kk < r) ? Fb[2 * kk] : 0.f;
+                tc_step(cc[nt], c2[nt], A, fa, fb);
+              }
+            }
+          }
+          // every slot below rcap is rewritten (zero past the rank)
+          if (g < G) {
+            typename T::W* dst = xpart + ((long long)c * dC + (d - 1)) * a.rcap * G + g;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+              const int kk = k0 + 8 * nt + 2 * tq;
+              if (kk < a.rcap)
+                T::store(dst + kk * G, T::pack(Cx<float>(cc[nt][0] + c2[nt][0], cc[nt][2] + c2[nt][2]), tag));
+              if (kk + 1 < a.rcap)
+                T::store(dst + (kk + 1) * G, T::pack(Cx<float>(cc[nt][1] + c2[nt][1], cc[nt][3] + c2[nt][3]), tag));
+            }
+          }
+        }
+      }
+    };
+
     if (ok1) {
-      reduce_items(0, dt[DT_WSTART + dC + 1], 0);
+      if (tc) reduce_anc_tc();
+      else reduce_items(0, dt[DT_WSTART + dC + 1], 0);
       reduce_items(dt[DT_WSTART + dC + 1], dt[DT_WSTART + L + 1], 1);
       constexpr int GJ = sizeof(R) == 4 ? 3 : 1;
       const int rg = a.rcap * G;
@@ -572,8 +665,76 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     __syncthreads();
     if (*s_fail != 0) break;
 
-    // ---- 4. expansion: lane = (row i, column slice ks) --------------------------------
-    {
+    // ---- 4. expansion ----------------------------------------------------------------
+    if (tc) {
+      if constexpr (kTC) {
+        // warps 0..3: the ancestors' terms on tensor cores, rows 16 w .. 16 w + 15 as two
+        // n-tiles, the columns of depths 1..dC as the k dimension; warps 4..11: the leaf
+        // block and the subtree depths on CUDA cores, four lanes per row
+        constexpr int KSL = 4;
+        Cx<R> yl[G];
+        int iloc = -1;
+        if (warp < 4) {
+          const int g = lane >> 2, tq = lane & 3, pp = tq & 1;
+          float cc[2][4] = {}, c2[2][4] = {};
+          const int rA = 16 * warp + g, rB = rA + 8;
+          for (int d = 1; d <= dC; ++d) {
+            const int r = trk[d - 1];
+            const Cx<float>* q = qanc + (d - 1) * a.rcap * GS;
+            const float* Fa = reinterpret_cast<const float*>(st + (rA < ns ? rowoff[d * SM + rA] : 0)) + pp;
+            const float* Fb = reinterpret_cast<const float*>(st + (rB < ns ? rowoff[d * SM + rB] : 0)) + pp;
+            for (int k0 = 0; k0 < r; k0 += 4) {
+              const int ka = k0 + (tq >> 1), kb = ka + 2;
+              const Cx<float> va = (ka < r && g < G) ? q[ka * GS + g] : Cx<float>(0.f, 0.f);
+              const Cx<float> vb = (kb < r && g < G) ? q[kb * GS + g] : Cx<float>(0.f, 0.f);
+              TcA A;
+              A.build(va, vb, pp);
+              tc_step(cc[0], c2[0], A, (rA < ns && ka < r) ? Fa[2 * ka] : 0.f, (rA < ns && kb < r) ? Fa[2 * kb] : 0.f);
+              tc_step(cc[1], c2[1], A, (rB < ns && ka < r) ? Fb[2 * ka] : 0.f, (rB < ns && kb < r) ? Fb[2 * kb] : 0.f);
+            }
+          }
+          if (g < G) {
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+              const int row = 16 * warp + 8 * nt + 2 * tq;
+              if (row < ns) ybuf[row * GS + g] = Cx<R>(cc[nt][0] + c2[nt][0], cc[nt][2] + c2[nt][2]);
+              if (row + 1 < ns) ybuf[(row + 1) * GS + g] = Cx<R>(cc[nt][1] + c2[nt][1], cc[nt][3] + c2[nt][3]);
+            }
+          }
+        } else if (warp < 4 + (64 * KSL) / 32) {
+          const int lt = tid - 128;
+          const int ks = lt % KSL;
+          const int i = lt / KSL;
+          typename M::A acc[G];
+#pragma unroll
+          for (int g = 0; g < G; ++g) M::zero(acc[g]);
+          if (i < ns) {
+            const int lam = s_leafnode[i];
+            const int j = lam - lam0;
+            const int ib = s_lo[lam] - lo_c;
+            const int* eb = erk + j * L1;
+            const int* ev = evo + j * L1;
+            expand_row<R, G, GS, KSL>(acc, st + rowoff[i], x + ib * GS, ks, eb[0]);
+            for (int d = dC + 1; d <= L; ++d)
+              expand_row<R, G, GS, KSL>(acc, st + rowoff[d * SM + i], reinterpret_cast<const Cx<R>*>(sm + ev[d]), ks,
+                                        eb[d]);
+          }
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            yl[g] = M::get(acc[g]);
+#pragma unroll
+            for (int o = 1; o < KSL; o <<= 1) yl[g] += shfl_xor(yl[g], o);
+          }
+          if (ks == 0 && i < ns) iloc = i;
+        }
+        __syncthreads();
+        if (iloc >= 0) {
+#pragma unroll
+          for (int g = 0; g < G; ++g) ybuf[iloc * GS + g] += yl[g];
+        }
+      }
+    } else {
+      // lane = (row i, column slice ks), all depths on CUDA cores
       const int nitems = ns * kKS;
       for (int item = tid; item < ((nitems + 31) & ~31); item += kThreads) {
         const bool live = item < nitems;
@@ -858,6 +1019,7 @@ static int apply_team_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
   a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.nnodes = h->nnodes; a.dC = cfg.dC; a.C = cfg.C;
   a.nteams = cfg.nteams; a.nrhs = nrhs; a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
   a.N = h->N; a.pack_stride = h->pack_stride;
+  a.tc = (sizeof(R) == 4 && a.slab_max <= 64 && h->opt.sweep_tc != 0) ? 1 : 0;
   a.lo = h->d_lo; a.sz = h->d_sz; a.rank = h->d_rank; a.recoff = h->d_recoff;
   a.pack = reinterpret_cast<const Cx<R>*>(h->d_pack);
   a.north = h->d_north; a.r = r; a.z = z;

@@ -133,3 +133,31 @@ def test_tma_sweeps_match_basic_sweep_and_exact(hs, n, prec, nrhs, team, kernel)
     assert e2 < tol, e2
     h1.free()
     h2.free()
+
+
+@pytest.mark.parametrize("n,nrhs,groups", [(255, 8, 0), (255, 5, 5), (255, 16, 0), (127, 3, 2)])
+def test_tensor_core_ancestor_terms_match_cuda_core_path(hs, n, nrhs, groups):
+    # complex64 team sweep: ancestor contractions on tensor cores (TF32 in three parts)
+    # against the same kernel with every contraction on CUDA cores, and the exact sweep
+    c, omega, pml = _problem(n, 5)
+    disc = Discretization(c, omega, pml)
+    R = torch.randn(nrhs, n * n, dtype=torch.complex128, device="cuda")
+    Z = {}
+    for tc in (1, 0):
+        h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6,
+                            hs.default_opts(precision=1, groups=groups, sweep_tc=tc))
+        assert h.sweep_plan(nrhs)["tma"] == 2
+        Z[tc] = h.apply(R)
+        torch.cuda.synchronize()
+        assert h.status()[0] == 0
+        if tc == 1:
+            T = []
+            for m in range(n):
+                lv, fac, rk = h.export_layer(m)
+                T.append(layer_to_dense(n, 8, 48, lv, fac, rk))
+        h.free()
+    err = (torch.linalg.norm(Z[1] - Z[0]) / torch.linalg.norm(Z[0])).item()
+    assert err < 2e-5, err
+    ref = solve_exact(disc, T, R[nrhs - 1].cpu().numpy())
+    e2 = np.linalg.norm(Z[1][nrhs - 1].cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert e2 < 2e-5, e2
