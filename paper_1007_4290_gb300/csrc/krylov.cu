@@ -15,27 +15,62 @@ namespace {
 
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs of partial sums per vector
 
-// partial[(s * nv + i) * B + b] = sum over block b's chunk of conj(V_i[s]) . w[s]
+constexpr int kDotChunk = 4;      // basis vectors per pass over w
+
+// partial[(s * nv + i) * B + b] = sum over block b's chunk of conj(V_i[s]) . w[s]; w is
+// read once per kDotChunk basis vectors
 __global__ void dots_kernel(const c128* const* __restrict__ V, int nv, const c128* __restrict__ w, long long N,
                             c128* __restrict__ partial) {
   const int s = blockIdx.y, B = gridDim.x;
   const long long chunk = (N + B - 1) / B;
   const long long beg = blockIdx.x * chunk, end = min(N, beg + chunk);
-  __shared__ c128 red[32];
+  __shared__ c128 red[kDotChunk][32];
   const c128* ws = w + s * N;
-  for (int i = 0; i < nv; ++i) {
-    const c128* vs = V[i] + s * N;
-    c128 acc(0, 0);
-    for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) cfma_conj(acc, vs[p], ws[p]);
-    for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      c128 t(0, 0);
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-      partial[((long long)s * nv + i) * B + blockIdx.x] = t;
+  for (int i0 = 0; i0 < nv; i0 += kDotChunk) {
+    const int nc = min(kDotChunk, nv - i0);
+    const c128* vs[kDotChunk];
+#pragma unroll
+    for (int i = 0; i < kDotChunk; ++i) vs[i] = V[i0 + (i < nc ? i : 0)] + s * N;
+    c128 acc[kDotChunk];
+#pragma unroll
+    for (int i = 0; i < kDotChunk; ++i) acc[i] = c128(0, 0);
+    for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) {
+      const c128 wp = ws[p];
+#pragma unroll
+      for (int i = 0; i < kDotChunk; ++i)
+        if (i < nc) cfma_conj(acc[i], vs[i][p], wp);
+    }
+#pragma unroll
+    for (int i = 0; i < kDotChunk; ++i) {
+      for (int o = 16; o > 0; o >>= 1) acc[i] += shfl_xor(acc[i], o);
+      if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = acc[i];
     }
     __syncthreads();
+    if (threadIdx.x < nc) {
+      c128 t(0, 0);
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+      partial[((long long)s * nv + i0 + threadIdx.x) * B + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// partial[s * B + b] = sum over block b's chunk of |x[s]|^2 (as the real part)
+__global__ void sqnorm_kernel(const c128* __restrict__ x, long long N, c128* __restrict__ partial) {
+  const int s = blockIdx.y, B = gridDim.x;
+  const long long chunk = (N + B - 1) / B;
+  const long long beg = blockIdx.x * chunk, end = min(N, beg + chunk);
+  __shared__ double red[32];
+  const c128* xs = x + s * N;
+  double acc = 0.0;
+  for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) acc += abs2(xs[p]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    partial[(long long)s * B + blockIdx.x] = c128(t, 0.0);
   }
 }
 
@@ -164,11 +199,7 @@ static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs,
 // ||x[s]|| for every s, on the host
 static int norms(hsweep_s* h, const c128* x, int nrhs, std::vector<double>& out) {
   KrylovWork* k = h->kw;
-  const c128* tbl[1] = {x};
-  // a one-entry table lives in the coef buffer (it is not in use while norms run)
-  HSW_CUDA(cudaMemcpyAsync(k->coef, tbl, sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
-  dots_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->coef), 1, x,
-                                                               h->N, k->partial);
+  sqnorm_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(x, h->N, k->partial);
   h->nlaunch += 1;
   reduce_partials<<<nrhs, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
   h->nlaunch += 1;
@@ -305,16 +336,25 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
   if ((rc = hsw_apply(h, f, k->z, nrhs))) return rc;
   if ((rc = norms(h, k->z, nrhs, Mfn))) return rc;
   if ((rc = norms(h, f, nrhs, fn))) return rc;
+  // with a zero initial guess the first residual is f itself and M r = M f is at hand
+  std::vector<double> un;
+  if ((rc = norms(h, u, nrhs, un))) return rc;
+  bool u_zero = true;
+  for (int s = 0; s < nrhs; ++s) u_zero = u_zero && un[s] == 0.0;
   std::vector<char> done(nrhs, 0);
   const int outer_max = h->opt.refine_max;
   bool all_done = false;
   for (int outer = 0; outer < outer_max && !all_done; ++outer) {
     // r = f - A u, z = M r
-    if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
-    sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
-    h->nlaunch += 1;
-    if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
-    if ((rc = norms(h, k->z, nrhs, zn))) return rc;
+    if (outer == 0 && u_zero) {
+      zn = Mfn;      // k->z still holds M f
+    } else {
+      if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
+      sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
+      h->nlaunch += 1;
+      if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
+      if ((rc = norms(h, k->z, nrhs, zn))) return rc;
+    }
     std::vector<char> active(nrhs, 0);
     std::vector<double> eta(nrhs, 0.0);
     all_done = true;
