@@ -214,6 +214,9 @@ def main():
     ap.add_argument("--apply-only", type=int, default=0, metavar="NRHS",
                     help="time only the sweep apply (Algorithm 2.6) on NRHS right-hand sides")
     ap.add_argument("--setup-only", action="store_true", help="time only the setup sweep (Algorithm 2.5)")
+    ap.add_argument("--team", type=int, default=0, help="with --apply-only: CTAs per sweep team (0 = automatic)")
+    ap.add_argument("--groups", type=int, default=0, help="with --apply-only: right-hand sides per team (0 = automatic)")
+    ap.add_argument("--sweep-tc", type=int, default=0, help="with --apply-only: ancestor contractions on tensor cores")
     args = ap.parse_args()
 
     if args.cpu_sample is not None:
@@ -403,7 +406,8 @@ def run_parts(args):
     prec = hs.FP64 if args.fp64 else hs.MIXED
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = hs.hsweep_setup(c_d, w["omega"], w["pml"], w["eps_H"], hs.default_opts(precision=prec))
+    h = hs.hsweep_setup(c_d, w["omega"], w["pml"], w["eps_H"],
+                        hs.default_opts(precision=prec, team=args.team, groups=args.groups, sweep_tc=args.sweep_tc))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     out = {"workload": args.workload, "n": n, "precision": "fp64" if args.fp64 else "mixed", "setup_s": setup_s,
