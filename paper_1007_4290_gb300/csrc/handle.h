@@ -1,5 +1,6 @@
 // Internal state of an hsweep handle, shared by the translation units of the library.
 #pragma once
+#include <array>
 #include <utility>
 #include <vector>
 #include "common.cuh"
@@ -64,6 +65,9 @@ struct hsweep_s {
   long long pack_stride = 0;             // entries per layer (worst-case capacity)
   long long* d_recoff = nullptr;         // [n][nleaves + 1] record offsets within a layer
   std::vector<long long> slab_bytes_max; // per slab depth dC: largest slab record in bytes
+  // team-sweep launch plans already chosen: {nrhs, ok, dC, C, G, teams, smem}; cleared
+  // whenever the packed factors change
+  std::vector<std::array<long long, 7>> team_plans;
   int rank_max = 0;
   bool pack_valid = false;
 

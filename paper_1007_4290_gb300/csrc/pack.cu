@@ -88,6 +88,7 @@ int hsw_pack(hsweep_s* h, int m0, int m1) {
   HSW_CUDA(cudaStreamSynchronize(h->stream));
   const size_t es = h->fac_elem();
   h->slab_bytes_max.assign(h->L + 1, 0);
+  h->team_plans.clear();
   for (int dC = 0; dC <= h->L; ++dC) {
     const int nl = 1 << (h->L - dC);
     long long mx = 0;

@@ -17,7 +17,7 @@
 //   4. expansion y_i = D x + sum_v F_v[i, :] q_sib(v): eight lanes per row, each over
 //      every eighth column, all G right-hand sides in registers;
 //   5. the update of Algorithm 2.6 for (row, right-hand side) pairs, one per thread,
-//      with coalesced global reads (prefetched at the start of the step) and writes;
+//      with coalesced global reads and writes;
 //      the row offsets and block tables of the next step's record.
 // Three block barriers per step; no team-wide barrier: a CTA waits only for the
 // partial sums it reads.  The tag is the lowest bit of every 8-byte word of a partial
@@ -256,15 +256,15 @@ __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const C
   }
 }
 
-template <typename R, int G>
+template <typename R, int G, bool TC>
 __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   using M = Mac<R>;
   using T = Tagged<R>;
   constexpr int GS = vstride<R>(G);
   constexpr int kUPT = upt(G);
-  constexpr bool kTC = std::is_same<R, float>::value;
-  const bool tc = kTC && a.tc != 0;
+  constexpr bool kTC = TC && std::is_same<R, float>::value;
+  constexpr bool tc = kTC;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n, L = a.L, dC = a.dC, nl = a.nl, lf = a.leaf, SM = a.slab_max;
   const int team = blockIdx.x / a.C, c = blockIdx.x % a.C;
@@ -451,27 +451,6 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
         x[i * GS + g] = v;
       }
       __syncthreads();
-    }
-    // the update's global inputs for this thread's (row, right-hand side) pairs
-    c128 pin[kUPT], pcpl[kUPT];
-    Cx<R> pw[kUPT];
-    {
-      const int mn = (fwd && m < n - 1) ? m + 1 : m;
-#pragma unroll
-      for (int u = 0; u < kUPT; ++u) {
-        const int p = tid + u * kThreads;
-        pin[u] = c128(0.0, 0.0);
-        pw[u] = Cx<R>(0, 0);
-        pcpl[u] = c128(0.0, 0.0);
-        if (p < ns * G) {
-          const int i = p % ns, g = p / ns;
-          pcpl[u] = a.north[(long long)mn * n + lo_c + i];
-          if (g < gcount) {
-            if (fwd && m < n - 1) pin[u] = a.r[(long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i];
-            else if (!fwd) pw[u] = a.w[(long long)(g0 + g) * a.N + (long long)m * n + lo_c + i];
-          }
-        }
-      }
     }
     {   // the stage of step t
       long long spins = 0;
@@ -770,25 +749,35 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
 
     // ---- 5. the update of Algorithm 2.6 for this thread's (row, rhs) pairs; the next
     //         step's row offsets ---------------------------------------------------------
+    // (its global inputs are loaded here: issuing them at the start of the step cost more
+    // issue stalls than their latency costs here)
 #pragma unroll
     for (int u = 0; u < kUPT; ++u) {
       const int p = tid + u * kThreads;
       if (p < ns * G) {
         const int i = p % ns, g = p / ns;
         const bool valid = g < gcount;
+        const int mn = (fwd && m < n - 1) ? m + 1 : m;
+        const c128 cpl2 = a.north[(long long)mn * n + lo_c + i];
+        c128 fin(0.0, 0.0);
+        Cx<R> win(0, 0);
+        if (valid) {
+          if (fwd && m < n - 1) fin = a.r[(long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i];
+          else if (!fwd) win = a.w[(long long)(g0 + g) * a.N + (long long)m * n + lo_c + i];
+        }
         const Cx<R> y = ybuf[i * GS + g];
-        const Cx<R> cpl = cvt<R>(pcpl[u]);
+        const Cx<R> cpl = cvt<R>(cpl2);
         const long long pos = (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
         if (fwd) {
           if (m < n - 1) {
             if (valid) a.w[pos] = y;
-            xn[i * GS + g] = cvt<R>(pin[u]) - cpl * y;
+            xn[i * GS + g] = cvt<R>(fin) - cpl * y;
           } else {
             if (valid) a.z[pos] = cvt<double>(y);
             xn[i * GS + g] = cpl * y;
           }
         } else {
-          const Cx<R> uu = valid ? pw[u] - y : Cx<R>(0, 0);
+          const Cx<R> uu = valid ? win - y : Cx<R>(0, 0);
           if (valid) a.z[pos] = cvt<double>(uu);
           if (m > 0) xn[i * GS + g] = cpl * uu;
         }
@@ -869,7 +858,7 @@ static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a) {
 
 template <typename R, int G>
 static int resident_ctas(const hsweep_s* h, size_t smem) {
-  auto kern = sweep_team_kernel<R, G>;
+  auto kern = sweep_team_kernel<R, G, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -897,7 +886,7 @@ static int resident_for(const hsweep_s* h, int G, size_t smem) {
 // steps, a step costing a fixed latency (exchange through L2, barriers) plus work that grows
 // with the slab's rows times G.
 template <typename R>
-static TeamConfig choose_team(const hsweep_s* h, int nrhs) {
+static TeamConfig choose_team_uncached(const hsweep_s* h, int nrhs) {
   TeamConfig best{};
   best.ok = false;
   double best_cost = 1e300;
@@ -929,9 +918,24 @@ static TeamConfig choose_team(const hsweep_s* h, int nrhs) {
   return best;
 }
 
+// the plan for nrhs, from the handle's cache when this nrhs was planned before (the
+// occupancy queries behind a plan cost more than a short apply)
+template <typename R>
+static TeamConfig choose_team(hsweep_s* h, int nrhs) {
+  for (const auto& e : h->team_plans)
+    if (e[0] == nrhs) return TeamConfig{e[1] != 0, (int)e[2], (int)e[3], (int)e[4], (int)e[5], (size_t)e[6]};
+  const TeamConfig c = choose_team_uncached<R>(h, nrhs);
+  if (h->team_plans.size() >= 64) h->team_plans.erase(h->team_plans.begin());
+  h->team_plans.push_back({nrhs, c.ok ? 1 : 0, c.dC, c.C, c.G, c.nteams, (long long)c.smem});
+  return c;
+}
+
 template <typename R, int G>
 static int launch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
-  auto kern = sweep_team_kernel<R, G>;
+  auto kern = sweep_team_kernel<R, G, false>;
+  if constexpr (sizeof(R) == 4) {
+    if (a.tc) kern = sweep_team_kernel<R, G, true>;
+  }
   HSW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
