@@ -85,7 +85,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
       opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
-      (opt.sweep_tc != 0 && opt.sweep_tc != 1))
+      opt.sweep_tc < 0 || opt.sweep_tc > 2)
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;

@@ -256,14 +256,15 @@ __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const C
   }
 }
 
-template <typename R, int G, bool TC>
+template <typename R, int G, int TC>
 __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   using M = Mac<R>;
   using T = Tagged<R>;
   constexpr int GS = vstride<R>(G);
   constexpr int kUPT = upt(G);
-  constexpr bool kTC = TC && std::is_same<R, float>::value;
+  constexpr bool kTC = TC > 0 && std::is_same<R, float>::value;    // reductions on tensor cores
+  constexpr bool kTCE = TC > 1 && std::is_same<R, float>::value;   // and the expansion
   constexpr bool tc = kTC;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n, L = a.L, dC = a.dC, nl = a.nl, lf = a.leaf, SM = a.slab_max;
@@ -612,13 +613,38 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
           for (int u = 0; u < 8; ++u)
             if (use[j] && u < span[j]) vals[j][u] = T::load(src[j] + u * cstride);
         }
+        // re-read every word not yet written for this step, all of them together per round
+        {
+          long long spins = 0;
+          for (;;) {
+            bool pending = false;
+#pragma unroll
+            for (int j = 0; j < GJ; ++j)
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (use[j] && u < span[j] && !T::ok(vals[j][u], tag)) {
+                  vals[j][u] = T::load(src[j] + u * cstride);
+                  pending = true;
+                }
+            if (!pending) break;
+            if (++spins > kWaitLimit || *(volatile int*)a.status != 0) {
+              report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
+              *s_fail = 1;
+              break;
+            }
+          }
+        }
 #pragma unroll
         for (int j = 0; j < GJ; ++j) {
           const int it = base + j * kThreads;
           if (it >= tot) continue;
           Cx<R> acc(0, 0);
           if (use[j]) {
-            auto settle = [&](typename T::W v, int u) {   // re-read until written for this step
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (u < span[j]) acc += T::value(vals[j][u]);
+            for (int u = 8; u < span[j]; ++u) {    // teams of more than 16 CTAs
+              typename T::W v = T::load(src[j] + u * cstride);
               long long spins = 0;
               while (!T::ok(v, tag)) {
                 if (++spins > kWaitLimit || *(volatile int*)a.status != 0) {
@@ -629,11 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
                 v = T::load(src[j] + u * cstride);
               }
               acc += T::value(v);
-            };
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (u < span[j]) settle(vals[j][u], u);
-            for (int u = 8; u < span[j]; ++u) settle(T::load(src[j] + u * cstride), u);
+            }
           }
           const int d = it / rg + 1;
           const int kg = it - (d - 1) * rg;
@@ -645,8 +667,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     if (*s_fail != 0) break;
 
     // ---- 4. expansion ----------------------------------------------------------------
-    if (tc) {
-      if constexpr (kTC) {
+    if (kTCE) {
+      if constexpr (kTCE) {
         // warps 0..3: the ancestors' terms on tensor cores, rows 16 w .. 16 w + 15 as two
         // n-tiles, the columns of depths 1..dC as the k dimension; warps 4..11: the leaf
         // block and the subtree depths on CUDA cores, four lanes per row
@@ -858,7 +880,7 @@ static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a) {
 
 template <typename R, int G>
 static int resident_ctas(const hsweep_s* h, size_t smem) {
-  auto kern = sweep_team_kernel<R, G, false>;
+  auto kern = sweep_team_kernel<R, G, 0>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -932,9 +954,10 @@ static TeamConfig choose_team(hsweep_s* h, int nrhs) {
 
 template <typename R, int G>
 static int launch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
-  auto kern = sweep_team_kernel<R, G, false>;
+  auto kern = sweep_team_kernel<R, G, 0>;
   if constexpr (sizeof(R) == 4) {
-    if (a.tc) kern = sweep_team_kernel<R, G, true>;
+    if (a.tc == 1) kern = sweep_team_kernel<R, G, 1>;
+    if (a.tc == 2) kern = sweep_team_kernel<R, G, 2>;
   }
   HSW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
   cudaLaunchConfig_t lc = {};
@@ -1023,7 +1046,7 @@ static int apply_team_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
   a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.nnodes = h->nnodes; a.dC = cfg.dC; a.C = cfg.C;
   a.nteams = cfg.nteams; a.nrhs = nrhs; a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
   a.N = h->N; a.pack_stride = h->pack_stride;
-  a.tc = (sizeof(R) == 4 && a.slab_max <= 64 && h->opt.sweep_tc != 0) ? 1 : 0;
+  a.tc = (sizeof(R) == 4 && a.slab_max <= 64) ? h->opt.sweep_tc : 0;
   a.lo = h->d_lo; a.sz = h->d_sz; a.rank = h->d_rank; a.recoff = h->d_recoff;
   a.pack = reinterpret_cast<const Cx<R>*>(h->d_pack);
   a.north = h->d_north; a.r = r; a.z = z;
