@@ -45,24 +45,65 @@ __global__ void assemble_kernel(int n, double h, double eta, double pref, double
   diag[p] = k2 - (((e_l + e_r) + n_l) + n_r);
 }
 
+// y[s] = A x[s] for right-hand sides s0 .. s0 + 7: one thread per node, the five
+// coefficients loaded once, the 8 x 5 neighbour values of all eight right-hand sides in
+// flight together
+constexpr int kMvRhs = 8;
+template <typename T>
 __global__ void matvec_kernel(int n, long long N, int nrhs, const c128* __restrict__ diag,
                               const c128* __restrict__ east, const c128* __restrict__ north,
                               const c128* __restrict__ x, c128* __restrict__ y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y;
-  if (i >= n) return;
-  long long p = (long long)j * n + i;
-  c128 d = diag[p];
-  c128 el = east[(long long)j * (n + 1) + i], er = east[(long long)j * (n + 1) + i + 1];
-  c128 nl = north[(long long)j * n + i], nr = north[(long long)(j + 1) * n + i];
-  for (int s = blockIdx.z; s < nrhs; s += gridDim.z) {
-    const c128* xs = x + s * N;
-    c128 acc = d * xs[p];
-    if (i > 0) cfma(acc, el, xs[p - 1]);
-    if (i < n - 1) cfma(acc, er, xs[p + 1]);
-    if (j > 0) cfma(acc, nl, xs[p - n]);
-    if (j < n - 1) cfma(acc, nr, xs[p + n]);
-    y[s * N + p] = acc;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int j = (int)(p / n), i = (int)(p - (long long)j * n);
+  const int s0 = blockIdx.y * kMvRhs;
+  const c128 zero(0.0, 0.0);
+  const Cx<T> d = cvt<T>(diag[p]);
+  const Cx<T> el = cvt<T>(i > 0 ? east[(long long)j * (n + 1) + i] : zero);
+  const Cx<T> er = cvt<T>(i < n - 1 ? east[(long long)j * (n + 1) + i + 1] : zero);
+  const Cx<T> nl = cvt<T>(j > 0 ? north[(long long)j * n + i] : zero);
+  const Cx<T> nr = cvt<T>(j < n - 1 ? north[(long long)(j + 1) * n + i] : zero);
+  const long long pl = i > 0 ? p - 1 : p, pr = i < n - 1 ? p + 1 : p;
+  const long long pd = j > 0 ? p - n : p, pu = j < n - 1 ? p + n : p;
+  Cx<T> v[kMvRhs][5];
+#pragma unroll
+  for (int u = 0; u < kMvRhs; ++u) {
+    if (s0 + u < nrhs) {
+      const c128* xs = x + (long long)(s0 + u) * N;
+      v[u][0] = cvt<T>(xs[p]);
+      v[u][1] = cvt<T>(xs[pl]);
+      v[u][2] = cvt<T>(xs[pr]);
+      v[u][3] = cvt<T>(xs[pd]);
+      v[u][4] = cvt<T>(xs[pu]);
+    }
+  }
+  // away from the PML every coefficient is real: complex x real multiply-adds give the
+  // same values with half the FP64 operations (FP64 throughput bounds this kernel)
+  const bool real_coef = d.im == 0.0 && el.im == 0.0 && er.im == 0.0 && nl.im == 0.0 && nr.im == 0.0;
+  if (real_coef) {
+#pragma unroll
+    for (int u = 0; u < kMvRhs; ++u) {
+      if (s0 + u < nrhs) {
+        T re = d.re * v[u][0].re, im = d.re * v[u][0].im;
+        re = fma(el.re, v[u][1].re, re); im = fma(el.re, v[u][1].im, im);
+        re = fma(er.re, v[u][2].re, re); im = fma(er.re, v[u][2].im, im);
+        re = fma(nl.re, v[u][3].re, re); im = fma(nl.re, v[u][3].im, im);
+        re = fma(nr.re, v[u][4].re, re); im = fma(nr.re, v[u][4].im, im);
+        y[(long long)(s0 + u) * N + p] = c128(re, im);
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < kMvRhs; ++u) {
+    if (s0 + u < nrhs) {
+      Cx<T> acc = d * v[u][0];
+      cfma(acc, el, v[u][1]);
+      cfma(acc, er, v[u][2]);
+      cfma(acc, nl, v[u][3]);
+      cfma(acc, nr, v[u][4]);
+      y[(long long)(s0 + u) * N + p] = cvt<double>(acc);
+    }
   }
 }
 
@@ -79,12 +120,18 @@ int hsw_assemble(hsweep_s* h, double pml_C, int pml_form) {
   return HSWEEP_OK;
 }
 
-int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs) {
+int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp) {
   if (nrhs <= 0) return HSWEEP_OK;
-  dim3 grid(div_up(h->n, 128), h->n, nrhs < 8 ? nrhs : 8);
-  matvec_kernel<<<grid, 128, 0, h->stream>>>(h->n, (long long)h->N, nrhs, h->d_diag, h->d_east,
-                                              h->d_north, x, y);
+  dim3 grid(div_up(h->N, 256), div_up(nrhs, kMvRhs));
+  if (lowp)
+    matvec_kernel<float><<<grid, 256, 0, h->stream>>>(h->n, (long long)h->N, nrhs, h->d_diag, h->d_east,
+                                                      h->d_north, x, y);
+  else
+    matvec_kernel<double><<<grid, 256, 0, h->stream>>>(h->n, (long long)h->N, nrhs, h->d_diag, h->d_east,
+                                                       h->d_north, x, y);
   h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   return HSWEEP_OK;
 }
+
+int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs) { return hsw_matvec_prec(h, x, y, nrhs, false); }

@@ -101,6 +101,8 @@ void hsw_release(hsweep_s* h, void* p);
 // assemble.cu
 int hsw_assemble(hsweep_s* h, double pml_C, int pml_form);
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
+// the same product with FP32 arithmetic (lowp) on the FP64 vectors
+int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp);
 // apply.cu
 int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs);
 size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs);

@@ -1,11 +1,15 @@
 // GMRES on the left-preconditioned system M A u = M f (Section 2.4), batched over
-// right-hand sides, with FP64 Arnoldi (classical Gram-Schmidt, applied twice), Givens
+// right-hand sides, with Arnoldi by classical Gram-Schmidt applied twice, Givens
 // rotations on the host, and an outer loop on the FP64 residual:
 //     r = f - A u,  z = M r,  stop when ||z|| <= tol ||M f||,
 //     otherwise GMRES on M A d = z (x0 = 0) and u += d.
 // In HSWEEP_FP64 a converged inner solve ends the loop (its residual estimate is the
 // FP64 one); in HSWEEP_MIXED, where M runs in complex64, every outer step re-checks
-// the FP64 residual (iterative refinement).
+// the FP64 residual (iterative refinement), and the inner GMRES computes in FP32 on
+// FP64-stored vectors (its target is a relative 4e-6 at most; the FP64 arithmetic units
+// of this GPU run at about 1/60 of the FP32 rate): per-thread products and partial sums
+// in FP32, block and global sums in FP64.  The residual f - A u, the update u += d and
+// the reported residuals stay FP64.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -18,7 +22,8 @@ constexpr int kRedBlocks = 304;   // 2 x 152 SMs of partial sums per vector
 constexpr int kDotChunk = 4;      // basis vectors per pass over w
 
 // partial[(s * nv + i) * B + b] = sum over block b's chunk of conj(V_i[s]) . w[s]; w is
-// read once per kDotChunk basis vectors
+// read once per kDotChunk basis vectors; T = the per-thread arithmetic type
+template <typename T>
 __global__ void dots_kernel(const c128* const* __restrict__ V, int nv, const c128* __restrict__ w, long long N,
                             c128* __restrict__ partial) {
   const int s = blockIdx.y, B = gridDim.x;
@@ -31,17 +36,19 @@ __global__ void dots_kernel(const c128* const* __restrict__ V, int nv, const c12
     const c128* vs[kDotChunk];
 #pragma unroll
     for (int i = 0; i < kDotChunk; ++i) vs[i] = V[i0 + (i < nc ? i : 0)] + s * N;
-    c128 acc[kDotChunk];
+    Cx<T> acct[kDotChunk];
 #pragma unroll
-    for (int i = 0; i < kDotChunk; ++i) acc[i] = c128(0, 0);
+    for (int i = 0; i < kDotChunk; ++i) acct[i] = Cx<T>(0, 0);
     for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) {
-      const c128 wp = ws[p];
+      const Cx<T> wp = cvt<T>(ws[p]);
 #pragma unroll
       for (int i = 0; i < kDotChunk; ++i)
-        if (i < nc) cfma_conj(acc[i], vs[i][p], wp);
+        if (i < nc) cfma_conj(acct[i], cvt<T>(vs[i][p]), wp);
     }
+    c128 acc[kDotChunk];
 #pragma unroll
     for (int i = 0; i < kDotChunk; ++i) {
+      acc[i] = cvt<double>(acct[i]);
       for (int o = 16; o > 0; o >>= 1) acc[i] += shfl_xor(acc[i], o);
       if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = acc[i];
     }
@@ -56,14 +63,16 @@ __global__ void dots_kernel(const c128* const* __restrict__ V, int nv, const c12
 }
 
 // partial[s * B + b] = sum over block b's chunk of |x[s]|^2 (as the real part)
+template <typename T>
 __global__ void sqnorm_kernel(const c128* __restrict__ x, long long N, c128* __restrict__ partial) {
   const int s = blockIdx.y, B = gridDim.x;
   const long long chunk = (N + B - 1) / B;
   const long long beg = blockIdx.x * chunk, end = min(N, beg + chunk);
   __shared__ double red[32];
   const c128* xs = x + s * N;
-  double acc = 0.0;
-  for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) acc += abs2(xs[p]);
+  T acct = T(0);
+  for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) acct += abs2(cvt<T>(xs[p]));
+  double acc = acct;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -89,27 +98,40 @@ __global__ void reduce_partials(const c128* __restrict__ partial, int B, c128* _
   }
 }
 
-// y[s] += sign * sum_i coef[s * ldc + i] * V_i[s]
+// y[s] += sign * sum_i coef[s * ldc + i] * V_i[s]; the basis pointers and coefficients of
+// the block's right-hand side are staged in shared memory, kAxpyMax at a time
+constexpr int kAxpyMax = 64;
+template <typename T>
 __global__ void axpy_multi(const c128* const* __restrict__ V, int nv, const c128* __restrict__ coef, int ldc,
                            double sign, c128* __restrict__ y, long long N) {
   const int s = blockIdx.y;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    c128 acc = y[s * N + p];
-    for (int i = 0; i < nv; ++i) {
-      c128 cf = coef[(long long)s * ldc + i];
-      cfma(acc, sign * cf, V[i][s * N + p]);
+  __shared__ const c128* sv[kAxpyMax];
+  __shared__ Cx<T> sc[kAxpyMax];
+  c128* ys = y + (long long)s * N;
+  for (int i0 = 0; i0 < nv; i0 += kAxpyMax) {
+    const int nc = min(kAxpyMax, nv - i0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+      sv[i] = V[i0 + i] + (long long)s * N;
+      sc[i] = cvt<T>(sign * coef[(long long)s * ldc + i0 + i]);
     }
-    y[s * N + p] = acc;
+    __syncthreads();
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+      Cx<T> acc = cvt<T>(ys[p]);
+      for (int i = 0; i < nc; ++i) cfma(acc, sc[i], cvt<T>(sv[i][p]));
+      ys[p] = cvt<double>(acc);
+    }
   }
 }
 
 // v[s] = w[s] / nrm[s] (zero when nrm[s] = 0)
+template <typename T>
 __global__ void scale_kernel(const c128* __restrict__ w, const double* __restrict__ nrm, c128* __restrict__ v,
                              long long N) {
   const int s = blockIdx.y;
-  const double a = nrm[s] > 0 ? 1.0 / nrm[s] : 0.0;
+  const T a = nrm[s] > 0 ? T(1.0 / nrm[s]) : T(0);
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
-    v[s * N + p] = a * w[s * N + p];
+    v[s * N + p] = cvt<double>(a * cvt<T>(w[s * N + p]));
 }
 
 // r = f - y
@@ -183,9 +205,11 @@ static int basis(hsweep_s* h, int i, c128** out) {
 }
 
 // dots[s * vmax + i] = <V_{first+i}[s], w[s]> for i < nv, copied to host hd (nrhs x nv)
-static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs, std::vector<std::complex<double>>& hd) {
+static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs, std::vector<std::complex<double>>& hd,
+                        bool lowp) {
   KrylovWork* k = h->kw;
-  dots_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(k->d_V + first, nv, w, h->N, k->partial);
+  if (lowp) dots_kernel<float><<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(k->d_V + first, nv, w, h->N, k->partial);
+  else dots_kernel<double><<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(k->d_V + first, nv, w, h->N, k->partial);
   h->nlaunch += 1;
   reduce_partials<<<nrhs * nv, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
   h->nlaunch += 1;
@@ -197,9 +221,10 @@ static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs,
 }
 
 // ||x[s]|| for every s, on the host
-static int norms(hsweep_s* h, const c128* x, int nrhs, std::vector<double>& out) {
+static int norms(hsweep_s* h, const c128* x, int nrhs, std::vector<double>& out, bool lowp = false) {
   KrylovWork* k = h->kw;
-  sqnorm_kernel<<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(x, h->N, k->partial);
+  if (lowp) sqnorm_kernel<float><<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(x, h->N, k->partial);
+  else sqnorm_kernel<double><<<dim3(kRedBlocks, nrhs), 256, 0, h->stream>>>(x, h->N, k->partial);
   h->nlaunch += 1;
   reduce_partials<<<nrhs, 256, 0, h->stream>>>(k->partial, kRedBlocks, k->dots);
   h->nlaunch += 1;
@@ -226,6 +251,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
   KrylovWork* k = h->kw;
   const int maxit = h->opt.gmres_max_it;
   const long long N = h->N;
+  const bool lowp = h->prec == HSWEEP_MIXED;   // FP32 arithmetic on FP64-stored vectors
   typedef std::complex<double> cd;
   std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(maxit + 1) * maxit, cd(0)));
   std::vector<std::vector<cd>> cs(nrhs, std::vector<cd>(maxit)), sn(nrhs, std::vector<cd>(maxit));
@@ -243,7 +269,8 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
   {
     std::vector<double> zn(znrm);
     HSW_CUDA(cudaMemcpyAsync(k->nrm, zn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    scale_kernel<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
+    if (lowp) scale_kernel<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
+    else scale_kernel<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
     h->nlaunch += 1;
   }
   std::vector<cd> hd, hd2;
@@ -256,21 +283,23 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     if ((rc = basis(h, j, &vj))) return rc;
     if ((rc = basis(h, j + 1, &vn))) return rc;
     // w = M (A v_j)
-    if ((rc = hsw_matvec(h, vj, k->t, nrhs))) return rc;
+    if ((rc = hsw_matvec_prec(h, vj, k->t, nrhs, lowp))) return rc;
     if ((rc = hsw_apply(h, k->t, k->w, nrhs))) return rc;
     // classical Gram-Schmidt, twice
     std::vector<cd> hcol((size_t)nrhs * (j + 1), cd(0));
     for (int pass = 0; pass < 2; ++pass) {
-      if ((rc = batched_dots(h, 0, j + 1, k->w, nrhs, hd))) return rc;
+      if ((rc = batched_dots(h, 0, j + 1, k->w, nrhs, hd, lowp))) return rc;
       for (size_t e = 0; e < hd.size(); ++e) hcol[e] += hd[e];
       HSW_CUDA(cudaMemcpyAsync(k->coef, hd.data(), hd.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
-      axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
+      if (lowp) axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
+      else axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
       h->nlaunch += 1;
     }
     std::vector<double> wn;
-    if ((rc = norms(h, k->w, nrhs, wn))) return rc;
+    if ((rc = norms(h, k->w, nrhs, wn, lowp))) return rc;
     HSW_CUDA(cudaMemcpyAsync(k->nrm, wn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    scale_kernel<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
+    if (lowp) scale_kernel<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
+    else scale_kernel<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
     h->nlaunch += 1;
     for (int s = 0; s < nrhs; ++s) {
       if (!run[s]) continue;
@@ -316,7 +345,8 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     for (int s = 0; s < nrhs; ++s)
       for (int i = 0; i < kmax; ++i) Yc[(size_t)s * kmax + i] = Y[(size_t)s * maxit + i];
     HSW_CUDA(cudaMemcpyAsync(k->coef, Yc.data(), Yc.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
-    axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
+    if (lowp) axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
+    else axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
     h->nlaunch += 1;
     HSW_CUDA(cudaGetLastError());
   }
@@ -334,7 +364,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
   std::vector<double> Mfn, fn, zn, est(nrhs, 1.0);
   // ||M f|| (the reference of the stopping test) and ||f||
   if ((rc = hsw_apply(h, f, k->z, nrhs))) return rc;
-  if ((rc = norms(h, k->z, nrhs, Mfn))) return rc;
+  if ((rc = norms(h, k->z, nrhs, Mfn, mixed))) return rc;
   if ((rc = norms(h, f, nrhs, fn))) return rc;
   // with a zero initial guess the first residual is f itself and M r = M f is at hand
   std::vector<double> un;
@@ -353,7 +383,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
       h->nlaunch += 1;
       if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
-      if ((rc = norms(h, k->z, nrhs, zn))) return rc;
+      if ((rc = norms(h, k->z, nrhs, zn, mixed))) return rc;
     }
     std::vector<char> active(nrhs, 0);
     std::vector<double> eta(nrhs, 0.0);
@@ -375,7 +405,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       const c128* tbl[1] = {k->d};
       HSW_CUDA(cudaMemcpyAsync(k->dots, tbl, sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
       HSW_CUDA(cudaMemcpyAsync(k->coef, one.data(), nrhs * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
-      axpy_multi<<<vec_grid(h, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->dots), 1,
+      axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->dots), 1,
                                                            k->coef, 1, 1.0, u, N);
       h->nlaunch += 1;
       HSW_CUDA(cudaGetLastError());
@@ -396,7 +426,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
   if ((rc = norms(h, k->r, nrhs, rn))) return rc;
   if (!all_done && mixed) {
     if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
-    if ((rc = norms(h, k->z, nrhs, zn))) return rc;
+    if ((rc = norms(h, k->z, nrhs, zn, mixed))) return rc;
     all_done = true;
     for (int s = 0; s < nrhs; ++s) if (!(zn[s] <= tol * Mfn[s])) all_done = false;
   }
