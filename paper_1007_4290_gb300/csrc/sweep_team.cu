@@ -767,28 +767,41 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
         }
       }
     }
+    // the update's global inputs for this thread's (row, rhs) pairs, issued before the
+    // barrier so that their latency overlaps the wait for the slowest warp (issued at the
+    // start of the step they cost more issue stalls than they saved)
+    c128 pcpl[kUPT], pin[kUPT];
+    Cx<R> pw[kUPT];
+#pragma unroll
+    for (int u = 0; u < kUPT; ++u) {
+      const int p = tid + u * kThreads;
+      pcpl[u] = c128(0.0, 0.0);
+      pin[u] = c128(0.0, 0.0);
+      pw[u] = Cx<R>(0, 0);
+      if (p < ns * G) {
+        const int i = p % ns, g = p / ns;
+        const int mn = (fwd && m < n - 1) ? m + 1 : m;
+        pcpl[u] = a.north[(long long)mn * n + lo_c + i];
+        if (g < gcount) {
+          if (fwd && m < n - 1) pin[u] = a.r[(long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i];
+          else if (!fwd) pw[u] = a.w[(long long)(g0 + g) * a.N + (long long)m * n + lo_c + i];
+        }
+      }
+    }
     __syncthreads();
 
     // ---- 5. the update of Algorithm 2.6 for this thread's (row, rhs) pairs; the next
     //         step's row offsets ---------------------------------------------------------
-    // (its global inputs are loaded here: issuing them at the start of the step cost more
-    // issue stalls than their latency costs here)
 #pragma unroll
     for (int u = 0; u < kUPT; ++u) {
       const int p = tid + u * kThreads;
       if (p < ns * G) {
         const int i = p % ns, g = p / ns;
         const bool valid = g < gcount;
-        const int mn = (fwd && m < n - 1) ? m + 1 : m;
-        const c128 cpl2 = a.north[(long long)mn * n + lo_c + i];
-        c128 fin(0.0, 0.0);
-        Cx<R> win(0, 0);
-        if (valid) {
-          if (fwd && m < n - 1) fin = a.r[(long long)(g0 + g) * a.N + (long long)(m + 1) * n + lo_c + i];
-          else if (!fwd) win = a.w[(long long)(g0 + g) * a.N + (long long)m * n + lo_c + i];
-        }
+        const c128 fin = pin[u];
+        const Cx<R> win = pw[u];
         const Cx<R> y = ybuf[i * GS + g];
-        const Cx<R> cpl = cvt<R>(cpl2);
+        const Cx<R> cpl = cvt<R>(pcpl[u]);
         const long long pos = (long long)(g0 + g) * a.N + (long long)m * n + lo_c + i;
         if (fwd) {
           if (m < n - 1) {
