@@ -68,6 +68,23 @@ def sweep_work(h, n, nrhs, elem_bytes):
     return flops, fac_bytes + vec_bytes, sum(lr) + n * leaf_e
 
 
+# DRAM bytes (read + write) of one sweep launch, from ncu captures summarised in profiles/,
+# keyed by workload and right-hand sides, with the SHA-256 of the kernel source they were
+# taken on: a changed kernel reports null instead of a stale number.
+SWEEP_TRAFFIC = {}
+TEAM_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_team.cu")
+
+
+def recorded_traffic(workload, nrhs):
+    rec = SWEEP_TRAFFIC.get("%s/%d" % (workload, nrhs))
+    if rec is None or not os.path.exists(TEAM_KERNEL_SRC):
+        return None
+    import hashlib
+    with open(TEAM_KERNEL_SRC, "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()
+    return rec["bytes"] if digest == rec["sha256"] else None
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -324,7 +341,7 @@ def main():
         roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = recorded_traffic(args.workload, nrhs)
     plan = h.sweep_plan(nrhs)
     roof["kernel"] = {2: "sweep_team_kernel", 1: "sweep_tma_kernel"}.get(plan["tma"], "sweep_kernel") + "<c64>"
     roof["plan"] = plan
