@@ -71,7 +71,11 @@ def sweep_work(h, n, nrhs, elem_bytes):
 # DRAM bytes (read + write) of one sweep launch, from ncu captures summarised in profiles/,
 # keyed by workload and right-hand sides, with the SHA-256 of the kernel source they were
 # taken on: a changed kernel reports null instead of a stale number.
-SWEEP_TRAFFIC = {}
+SWEEP_TRAFFIC = {
+    # profiles/sweep_team_n1023_random_64rhs_dram.md: 3.97 GB read + 1.57 GB written
+    "n1023_random/64": {"sha256": "75467c6fcf28dfa9fd94fa0d13c92a263363a102bddc6ec57678f988fd9e60fa",
+                        "bytes": 5.54e9},
+}
 TEAM_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_team.cu")
 
 

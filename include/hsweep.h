@@ -76,10 +76,10 @@ typedef struct {
                            first whose shared-memory plan fits;
                         1: the basic sweep that reads the factors from global memory;
                         2: the TMA-staged sweep on thread-block clusters (else basic) */
-  int sweep_tc;      /* 1: in HSWEEP_MIXED the team sweep computes the ancestor-level
-                        contractions with mma.sync tensor-core instructions (TF32 operands
-                        in three parts, FP32 accumulation); 0: on CUDA cores (default,
-                        faster on GB300: see the design notes) */
+  int sweep_tc;      /* HSWEEP_MIXED team sweep, ancestor-level contractions: 0 on CUDA cores
+                        (default, the faster on GB300); 1 the reductions, 2 the reductions
+                        and the expansion, with mma.sync tensor-core instructions (TF32
+                        operands in three parts, FP32 accumulation) */
 } hsweep_opts;
 
 /* Fill *o with the defaults listed above. */
