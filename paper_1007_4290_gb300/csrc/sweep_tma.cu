@@ -13,9 +13,11 @@
 //     columns k (contiguous in a row-major row), expansions y_i = sum_k F_v[i, k] q[k]
 //     with lanes over rows (odd row strides: no bank conflicts), four right-hand sides
 //     per thread from vector broadcast loads;
-//   - the ancestors' partial sums are exchanged through distributed shared memory
-//     inside the thread-block cluster (one hardware cluster barrier per step), or
-//     through L2 with a bounded-spin grid barrier when the team is the whole grid.
+//   - the ancestors' partial sums are exchanged through L2 (st.cg / ld.cg), ordered by
+//     one hardware cluster barrier per step when the team is a thread-block cluster, or
+//     by a bounded-spin grid barrier when the team is the whole grid.
+// (The default apply uses sweep_team.cu; this kernel is selected by sweep_kernel = 2 or
+// when the cooperative-team plan does not fit.)
 #include <cooperative_groups.h>
 #include "handle.h"
 #include "tma.cuh"
