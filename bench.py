@@ -238,6 +238,9 @@ def main():
     ap.add_argument("--team", type=int, default=0, help="with --apply-only: CTAs per sweep team (0 = automatic)")
     ap.add_argument("--groups", type=int, default=0, help="with --apply-only: right-hand sides per team (0 = automatic)")
     ap.add_argument("--sweep-tc", type=int, default=0, help="with --apply-only: ancestor contractions on tensor cores")
+    ap.add_argument("--direction-table", default="",
+                    help="comma-separated n (e.g. 127,255,511): GMRES steps and times of the upward and "
+                         "downward sweeps on the sweeping-direction workload (Section 3.1), one JSON line")
     args = ap.parse_args()
 
     if args.cpu_sample is not None:
@@ -250,6 +253,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.direction_table:
+        run_direction_table(args)
         return
     if args.apply_only or args.setup_only:
         run_parts(args)
@@ -415,6 +421,38 @@ def main():
     h.free()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_direction_table(args):
+    """The sweeping-direction test of Section 3.1 (c = 1/2 + x2, point source at
+    (0.125, 0.5), q = 8, fixed rank R = 2, GMRES tolerance 1e-3, FP64): setup and solve
+    times and GMRES steps of the upward (+x2) and downward (-x2) sweeps, per n."""
+    import torch
+    import paper_1007_4290_gb300 as hs
+    rows = []
+    for n in [int(v) for v in args.direction_table.split(",")]:
+        w = synth.workload("dir_n%d" % n)
+        f = torch.tensor(w["f"].reshape(1, -1), device="cuda")
+        row = {"n": n, "omega_over_2pi": w["omega"] / (2 * np.pi), "R": w["r_max"]}
+        for direction, key in ((1, "up"), (-1, "down")):
+            opts = hs.default_opts(precision=hs.FP64, r_max=w["r_max"], sweep_dir=direction)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], w["eps_H"], opts)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            u = torch.zeros_like(f)
+            h.solve(f, w["tol"], u=u, check=False)
+            u.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, it, rr = h.solve(f, w["tol"], u=u, check=False)
+            torch.cuda.synchronize()
+            row[key] = {"setup_s": t_setup, "solve_s": time.perf_counter() - t0, "iters": it[0], "relres": rr[0]}
+            h.free()
+        rows.append(row)
+    print(json.dumps({"metric": "GMRES steps, sweeping-direction test (Section 3.1), FP64, R = 2, tol 1e-3",
+                      "data": "synthetic", "rows": rows}))
 
 
 def run_parts(args):

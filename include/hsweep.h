@@ -80,6 +80,15 @@ typedef struct {
                         (default, the faster on GB300); 1 the reductions, 2 the reductions
                         and the expansion, with mma.sync tensor-core instructions (TF32
                         operands in three parts, FP32 accumulation) */
+  int sweep_dir;     /* +1 (default): the sweep runs over the layers from x2 = 0 upward
+                        (Algorithms 2.5/2.6); -1: from x2 = 1 downward (Section 3.1, the
+                        dependence on the sweeping direction).  A downward handle factors
+                        the reflected problem (velocity c(x1, 1 - x2)); hsweep_apply, _matvec,
+                        _solve and _grad take and return vectors in the caller's orientation
+                        (through device scratch of 2 * nrhs * n*n complex128 values, allocated
+                        on first use); layer m of hsweep_export_layer / _import_layer /
+                        _layer_ranks is the m-th layer of the sweep order; hsweep_apply_noalloc
+                        returns HSWEEP_ERR_ARG */
 } hsweep_opts;
 
 /* Fill *o with the defaults listed above. */

@@ -33,7 +33,8 @@ class hsweep_opts(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("r_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("pml_C", ctypes.c_double), ("pml_form", ctypes.c_int), ("gmres_max_it", ctypes.c_int),
                 ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int),
-                ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int)]
+                ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int),
+                ("sweep_dir", ctypes.c_int)]
 
 
 class HSweepError(RuntimeError):

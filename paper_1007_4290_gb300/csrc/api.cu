@@ -51,6 +51,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->groups = 0;
   o->sweep_kernel = 0;
   o->sweep_tc = 0;
+  o->sweep_dir = 1;
   return HSWEEP_OK;
 }
 
@@ -85,7 +86,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
       opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
-      opt.sweep_tc < 0 || opt.sweep_tc > 2)
+      opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
+      (opt.sweep_dir != 1 && opt.sweep_dir != -1))
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -104,6 +106,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   h->nleaves = h->tree.nleaves;
   h->r_max = opt.r_max;
   h->prec = opt.precision;
+  h->dir = opt.sweep_dir;
   int rc = HSWEEP_OK;
 #define TRY(x) do { rc = (x); if (rc != HSWEEP_OK) { destroy(h); return rc; } } while (0)
 #define TRYC(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); destroy(h); return HSWEEP_ERR_CUDA; } } while (0)
@@ -150,7 +153,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   TRYC(cudaMemsetAsync(h->d_recoff, 0, (size_t)n * (h->nleaves + 1) * sizeof(long long), h->stream));
   TRYC(cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), h->stream));
   TRYC(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
-  TRYC(cudaMemcpyAsync(h->d_c, c_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->dir < 0) TRY(hsw_flip_real(h, c_dev, h->d_c));   // the reflected problem
+  else TRYC(cudaMemcpyAsync(h->d_c, c_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   // the velocity must be finite and positive
   {
     std::vector<double> hc(N);
@@ -203,7 +207,15 @@ extern "C" int hsweep_apply(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs
   const char* zb = (const char*)z;
   size_t bytes = (size_t)nrhs * h->N * sizeof(hsw_c128);
   if (nrhs > 0 && rb < zb + bytes && zb < rb + bytes) return HSWEEP_ERR_ARG;
-  return hsw_apply(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs);
+  if (h->dir > 0 || nrhs == 0) return hsw_apply(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs);
+  // downward sweep: z = P M' P r with M' the upward sweep of the reflected problem
+  int rc = hsw_flip_reserve(h, 2 * bytes);
+  if (rc) return rc;
+  c128* a = static_cast<c128*>(h->d_flip);
+  c128* b = a + (size_t)nrhs * h->N;
+  if ((rc = hsw_flip_c128(h, reinterpret_cast<const c128*>(r), a, nrhs))) return rc;
+  if ((rc = hsw_apply(h, a, b, nrhs))) return rc;
+  return hsw_flip_c128(h, b, reinterpret_cast<c128*>(z), nrhs);
 }
 
 extern "C" int hsweep_matvec(hsweep_t h, const hsw_c128* x, hsw_c128* y, int nrhs) {
@@ -212,23 +224,58 @@ extern "C" int hsweep_matvec(hsweep_t h, const hsw_c128* x, hsw_c128* y, int nrh
   const char* yb = (const char*)y;
   size_t bytes = (size_t)nrhs * h->N * sizeof(hsw_c128);
   if (nrhs > 0 && xb < yb + bytes && yb < xb + bytes) return HSWEEP_ERR_ARG;
-  return hsw_matvec(h, reinterpret_cast<const c128*>(x), reinterpret_cast<c128*>(y), nrhs);
+  if (h->dir > 0 || nrhs == 0) return hsw_matvec(h, reinterpret_cast<const c128*>(x), reinterpret_cast<c128*>(y), nrhs);
+  int rc = hsw_flip_reserve(h, 2 * bytes);
+  if (rc) return rc;
+  c128* a = static_cast<c128*>(h->d_flip);
+  c128* b = a + (size_t)nrhs * h->N;
+  if ((rc = hsw_flip_c128(h, reinterpret_cast<const c128*>(x), a, nrhs))) return rc;
+  if ((rc = hsw_matvec(h, a, b, nrhs))) return rc;
+  return hsw_flip_c128(h, b, reinterpret_cast<c128*>(y), nrhs);
 }
 
 extern "C" int hsweep_solve(hsweep_t h, const hsw_c128* f, hsw_c128* u, int nrhs, double tol,
                             int* iters_out, double* relres_out) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!f || !u)) || !(tol > 0) || tol >= 1) return HSWEEP_ERR_ARG;
   if (nrhs == 0) return HSWEEP_OK;
-  return hsw_solve(h, reinterpret_cast<const c128*>(f), reinterpret_cast<c128*>(u), nrhs, tol,
-                   iters_out, relres_out);
+  if (h->dir > 0)
+    return hsw_solve(h, reinterpret_cast<const c128*>(f), reinterpret_cast<c128*>(u), nrhs, tol,
+                     iters_out, relres_out);
+  const size_t bytes = (size_t)nrhs * h->N * sizeof(c128);
+  int rc = hsw_flip_reserve(h, 2 * bytes);
+  if (rc) return rc;
+  c128* a = static_cast<c128*>(h->d_flip);
+  c128* b = a + (size_t)nrhs * h->N;
+  if ((rc = hsw_flip_c128(h, reinterpret_cast<const c128*>(f), a, nrhs))) return rc;
+  if ((rc = hsw_flip_c128(h, reinterpret_cast<const c128*>(u), b, nrhs))) return rc;
+  const int rs = hsw_solve(h, a, b, nrhs, tol, iters_out, relres_out);
+  if (rs != HSWEEP_OK && rs != HSWEEP_ERR_NOT_CONVERGED) return rs;
+  if ((rc = hsw_flip_c128(h, b, reinterpret_cast<c128*>(u), nrhs))) return rc;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HSWEEP_ERR_CUDA;
+  return rs;
 }
 
 extern "C" int hsweep_grad(hsweep_t h, const hsw_c128* f, int nsrc, const int* rec_idx, int nrec,
                            const hsw_c128* d, double* grad, double* misfit_out, double tol) {
   if (!h || nsrc < 1 || nrec < 1 || !f || !rec_idx || !d || !grad || !(tol > 0) || tol >= 1)
     return HSWEEP_ERR_ARG;
-  return hsw_grad(h, reinterpret_cast<const c128*>(f), nsrc, rec_idx, nrec,
-                  reinterpret_cast<const c128*>(d), grad, misfit_out, tol);
+  if (h->dir > 0)
+    return hsw_grad(h, reinterpret_cast<const c128*>(f), nsrc, rec_idx, nrec,
+                    reinterpret_cast<const c128*>(d), grad, misfit_out, tol);
+  // the reflected problem: sources and receiver nodes through P, the gradient back
+  const size_t fb = (size_t)nsrc * h->N * sizeof(c128);
+  const size_t rb = ((size_t)nrec * sizeof(int) + 255) / 256 * 256;
+  int rc = hsw_flip_reserve(h, fb + rb + (size_t)h->N * sizeof(double));
+  if (rc) return rc;
+  c128* fa = static_cast<c128*>(h->d_flip);
+  int* ra = reinterpret_cast<int*>(static_cast<unsigned char*>(h->d_flip) + fb);
+  double* ga = reinterpret_cast<double*>(static_cast<unsigned char*>(h->d_flip) + fb + rb);
+  if ((rc = hsw_flip_c128(h, reinterpret_cast<const c128*>(f), fa, nsrc))) return rc;
+  if ((rc = hsw_flip_index(h, rec_idx, ra, nrec))) return rc;
+  if ((rc = hsw_grad(h, fa, nsrc, ra, nrec, reinterpret_cast<const c128*>(d), ga, misfit_out, tol))) return rc;
+  if ((rc = hsw_flip_real(h, ga, grad))) return rc;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HSWEEP_ERR_CUDA;
+  return HSWEEP_OK;
 }
 
 extern "C" int hsweep_status(hsweep_t h, int* layer_out) {

@@ -29,7 +29,12 @@ struct Tree {
   int maxsz(int d) const { return (n + (1 << d) - 1) >> d; }
 };
 
-struct SetupWork;   // setup.cu
+struct SetupWork;   // direction.cu: reversal of the layer order (x2 -> 1 - x2)
+int hsw_flip_reserve(hsweep_s* h, size_t bytes);
+int hsw_flip_c128(hsweep_s* h, const c128* in, c128* out, int nvec);
+int hsw_flip_real(hsweep_s* h, const double* in, double* out);
+int hsw_flip_index(hsweep_s* h, const int* in, int* out, int cnt);
+// setup.cu
 struct KrylovWork;  // krylov.cu
 
 struct hsweep_s {
@@ -79,6 +84,12 @@ struct hsweep_s {
   void* d_xch = nullptr;       // team exchange slots
   long long wcache_cap = 0, xch_cap = 0;
 
+  // sweep direction: +1 upward from x2 = 0 (Algorithm 2.5), -1 downward (the handle holds
+  // the reflected problem; direction.cu) with a scratch for the reflected vectors
+  int dir = 1;
+  void* d_flip = nullptr;
+  size_t flip_cap = 0;
+
   SetupWork* sw = nullptr;
   KrylovWork* kw = nullptr;
 
@@ -119,6 +130,11 @@ int hsw_apply_team(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, vo
                    size_t scratch_bytes = 0);
 size_t hsw_apply_team_scratch_bytes(hsweep_s* h, int nrhs);
 int hsw_team_plan(hsweep_s* h, int nrhs, long long* out8);   // 1 if the team kernel would run
+// direction.cu: reversal of the layer order (x2 -> 1 - x2)
+int hsw_flip_reserve(hsweep_s* h, size_t bytes);
+int hsw_flip_c128(hsweep_s* h, const c128* in, c128* out, int nvec);
+int hsw_flip_real(hsweep_s* h, const double* in, double* out);
+int hsw_flip_index(hsweep_s* h, const int* in, int* out, int cnt);
 // setup.cu
 int hsw_factor(hsweep_s* h);
 void hsw_setup_free(hsweep_s* h);

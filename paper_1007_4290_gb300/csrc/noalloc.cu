@@ -39,6 +39,7 @@ int scratch_address(int dev, void** out) {
 
 extern "C" int hsweep_apply_noalloc(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!r || !z))) return HSWEEP_ERR_ARG;
+  if (h->dir < 0) return HSWEEP_ERR_ARG;   // a downward sweep needs reflected copies of r and z
   if (nrhs == 0) return HSWEEP_OK;
   const char* rb = (const char*)r;
   const char* zb = (const char*)z;

@@ -66,6 +66,12 @@ def velocity_random(n, width, seed, amp=0.2):
     return 1.0 + amp * smooth_noise(n, width, seed)
 
 
+def velocity_linear_x2(n, c0=0.5, slope=1.0):
+    """c(x1, x2) = c0 + slope * x2 (rows are x2, columns x1)."""
+    x, _ = grid(n)
+    return np.tile((c0 + slope * x)[:, None], (1, n))
+
+
 def source_gaussian(n, center=(0.5, 0.5), sigma=1.0 / 64.0):
     """Unnormalised Gaussian f = exp(-|x - x0|^2 / (2 sigma^2)) (complex128)."""
     x, _ = grid(n)
@@ -132,4 +138,11 @@ def workload(name):
         c = c_true + 0.05 * smooth_noise(n, 1 / 32, 3)
         return dict(name=name, n=n, omega=two_pi * 32, pml=pml, eps_H=1e-6, tol=1e-8,
                     c=c, c_true=c_true, f=f, rec_idx=rec_idx)
+    if name.startswith("dir_n"):
+        # the sweeping-direction test of Section 3.1: c = 1/2 + x2, a narrow Gaussian point
+        # source at (0.125, 0.5), q = 8 points per wavelength, fixed rank R = 2 (r_max = 2,
+        # no truncation threshold), GMRES tolerance 1e-3; PML one wavelength (8 cells)
+        n = int(name[len("dir_n"):])
+        return dict(name=name, n=n, omega=two_pi * (n + 1) / 8.0, pml=8, eps_H=0.0, r_max=2, tol=1e-3,
+                    c=velocity_linear_x2(n), f=source_gaussian(n, (0.125, 0.5))[None])
     raise KeyError(name)

@@ -130,3 +130,23 @@ def test_second_order_convergence_to_smooth_solution(with_pml):
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(rates > 1.8), (errs, rates)
     assert errs[-1] < 1e-3
+
+
+@pytest.mark.parametrize("n,pml", [(15, 3), (32, 5)])
+def test_reflection_in_x2_maps_the_operator_onto_itself(n, pml):
+    # The downward sweep (Section 3.1) factors the problem of the reflected velocity
+    # c(x1, 1 - x2): its operator must be P A P, with P the reversal of the layer order,
+    # and its solution the reflection of A^{-1} f.  The PML and the grid x = (k+1) h are
+    # symmetric under x2 -> 1 - x2 (up to rounding of the node coordinates).
+    c = synth.velocity_random(n, 1 / 8, 7)
+    omega = 2 * np.pi * (n + 1) / 10
+    A = Discretization(c, omega, pml).matrix().toarray()
+    Ar = Discretization(c[::-1, :].copy(), omega, pml).matrix().toarray()
+    perm = (np.arange(n)[::-1, None] * n + np.arange(n)[None, :]).ravel()
+    PAP = A[np.ix_(perm, perm)]
+    assert np.max(np.abs(Ar - PAP)) <= 1e-12 * np.max(np.abs(A))
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal(n * n) + 1j * rng.standard_normal(n * n)
+    u = SparseLU(Discretization(c, omega, pml)).solve(f)
+    ur = SparseLU(Discretization(c[::-1, :].copy(), omega, pml)).solve(f[perm])
+    assert np.linalg.norm(ur[perm] - u) <= 1e-10 * np.linalg.norm(u)
