@@ -150,3 +150,44 @@ def test_reflection_in_x2_maps_the_operator_onto_itself(n, pml):
     u = SparseLU(Discretization(c, omega, pml)).solve(f)
     ur = SparseLU(Discretization(c[::-1, :].copy(), omega, pml)).solve(f[perm])
     assert np.linalg.norm(ur[perm] - u) <= 1e-10 * np.linalg.norm(u)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_dirichlet_data_on_top_matches_the_closed_form(k):
+    # Section 2.5: non-zero Dirichlet data u(x1, 1) = b(x1) becomes a forcing term on the
+    # last layer.  Constant c, no PML on any side, f = 0, b = sin(k pi x1): the discrete
+    # solution is sin(k pi x_i) phi_j with phi_{j+1} + phi_{j-1} = 2 cos(theta) phi_j,
+    # phi_0 = 0, phi_{n+1} = 1, i.e. phi_j = sin(theta j) / sin(theta (n+1)), where
+    # cos(theta) = 1 - h^2 (omega^2/c^2 - lambda_k)/2 and lambda_k = (4/h^2) sin^2(k pi h/2).
+    n, c0 = 31, 1.0
+    h = 1.0 / (n + 1)
+    omega = 2 * np.pi * 3.3
+    x = (np.arange(n) + 1.0) * h
+    disc = Discretization(np.full((n, n), c0), omega, 6, pml_sides=0)
+    b = np.sin(k * np.pi * x)
+    f = disc.boundary_rhs(3, b)
+    u = SparseLU(disc).solve(f.ravel()).reshape(n, n)
+    lam = 4.0 / h ** 2 * np.sin(k * np.pi * h / 2) ** 2
+    theta = np.arccos(complex(1.0 - h * h * (omega ** 2 / c0 ** 2 - lam) / 2))
+    j = np.arange(1, n + 1)
+    phi = np.sin(theta * j) / np.sin(theta * (n + 1))
+    exact = phi[:, None] * np.sin(k * np.pi * x)[None, :]
+    assert np.max(np.abs(u - exact)) <= 1e-10 * np.max(np.abs(exact))
+
+
+def test_pml_side_mask():
+    # all four sides reproduce the default operator; no side equals no layer at all;
+    # a layer on x1 = 0 only is the mirror image (x1 -> 1 - x1) of a layer on x1 = 1 only
+    n, pml = 24, 5
+    c = synth.velocity_random(n, 1 / 6, 11)
+    omega = 2 * np.pi * 4.1
+    A = Discretization(c, omega, pml).matrix()
+    assert (Discretization(c, omega, pml, pml_sides=15).matrix() != A).nnz == 0
+    assert (Discretization(c, omega, pml, pml_sides=0).matrix() != Discretization(c, omega, 0).matrix()).nnz == 0
+    A_left = Discretization(c, omega, pml, pml_sides=1).matrix().toarray()
+    A_right = Discretization(c[:, ::-1].copy(), omega, pml, pml_sides=2).matrix().toarray()
+    perm = (np.arange(n)[:, None] * n + np.arange(n)[::-1][None, :]).ravel()
+    assert np.max(np.abs(A_left - A_right[np.ix_(perm, perm)])) <= 1e-12 * np.max(np.abs(A_left))
+    for sides in (1, 6, 9):
+        M = Discretization(c, omega, pml, pml_sides=sides).matrix()
+        assert abs(M - M.T).max() == 0
