@@ -238,6 +238,9 @@ def main():
     ap.add_argument("--team", type=int, default=0, help="with --apply-only: CTAs per sweep team (0 = automatic)")
     ap.add_argument("--groups", type=int, default=0, help="with --apply-only: right-hand sides per team (0 = automatic)")
     ap.add_argument("--sweep-tc", type=int, default=0, help="with --apply-only: ancestor contractions on tensor cores")
+    ap.add_argument("--boundary-table", default="",
+                    help="comma-separated n: GMRES steps and times of the boundary-condition examples of "
+                         "Section 3.2 (depth extrapolation, mixed PML / Dirichlet), one JSON line")
     ap.add_argument("--direction-table", default="",
                     help="comma-separated n (e.g. 127,255,511): GMRES steps and times of the upward and "
                          "downward sweeps on the sweeping-direction workload (Section 3.1), one JSON line")
@@ -256,6 +259,9 @@ def main():
         return
     if args.direction_table:
         run_direction_table(args)
+        return
+    if args.boundary_table:
+        run_boundary_table(args)
         return
     if args.apply_only or args.setup_only:
         run_parts(args)
@@ -452,6 +458,41 @@ def run_direction_table(args):
             h.free()
         rows.append(row)
     print(json.dumps({"metric": "GMRES steps, sweeping-direction test (Section 3.1), FP64, R = 2, tol 1e-3",
+                      "data": "synthetic", "rows": rows}))
+
+
+def run_boundary_table(args):
+    """The boundary-condition examples of Section 3.2 (q = 8, fixed rank R = 2, tol 1e-3,
+    FP64, upward sweep): depth extrapolation in a waveguide with Dirichlet data on x2 = 1
+    (b = 1 and a slant wave), and c = 1 with zero Dirichlet on x1 = 0, 1 (mixed1) or on
+    x1 = 1 and x2 = 1 (mixed2), a PML on the other sides."""
+    import torch
+    import paper_1007_4290_gb300 as hs
+    rows = []
+    for n in [int(v) for v in args.boundary_table.split(",")]:
+        row = {"n": n}
+        for kind in ("depth1", "depth2", "mixed1", "mixed2"):
+            w = synth.workload("%s_n%d" % (kind, n))
+            opts = hs.default_opts(precision=hs.FP64, r_max=w["r_max"], pml_sides=w["pml_sides"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], w["eps_H"], opts)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            f0 = torch.tensor(w["f"].reshape(1, -1), device="cuda")
+            if "b_top" in w:
+                h.boundary_rhs(3, torch.tensor(w["b_top"], device="cuda"), f0)
+            u = torch.zeros_like(f0)
+            h.solve(f0, w["tol"], u=u, check=False)
+            u.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, it, rr = h.solve(f0, w["tol"], u=u, check=False)
+            torch.cuda.synchronize()
+            row[kind] = {"setup_s": t_setup, "solve_s": time.perf_counter() - t0, "iters": it[0], "relres": rr[0]}
+            h.free()
+        rows.append(row)
+    print(json.dumps({"metric": "GMRES steps, boundary-condition examples (Section 3.2), FP64, R = 2, tol 1e-3",
                       "data": "synthetic", "rows": rows}))
 
 

@@ -89,6 +89,14 @@ typedef struct {
                         on first use); layer m of hsweep_export_layer / _import_layer /
                         _layer_ranks is the m-th layer of the sweep order; hsweep_apply_noalloc
                         returns HSWEEP_ERR_ARG */
+  int pml_sides;     /* bit mask of the sides with a PML: 1 x1 = 0, 2 x1 = 1, 4 x2 = 0, 8 x2 = 1
+                        (default 15, all four); a side without one is a Dirichlet boundary
+                        (Section 2.5), zero unless data is moved in by hsweep_boundary_rhs.
+                        hsweep_setup requires a PML on the side where the sweep starts
+                        (x2 = 0 upward, x2 = 1 downward) and returns HSWEEP_ERR_ARG otherwise:
+                        next to a Dirichlet side the first Schur complements have no
+                        absorption (a downward sweep of the depth-extrapolation problem met
+                        the GMRES test with a wrong solution in testing) */
 } hsweep_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -160,6 +168,19 @@ HSWEEP_API int hsweep_solve(hsweep_t h, const hsw_c128* f, hsw_c128* u, int nrhs
  */
 HSWEEP_API int hsweep_grad(hsweep_t h, const hsw_c128* f, int nsrc, const int* rec_idx, int nrec,
                 const hsw_c128* d, double* grad, double* misfit_out, double tol);
+
+/*
+ * Non-zero Dirichlet data on one side (Section 2.5, other boundary conditions; e.g. the
+ * depth extrapolation problem, u(x1, 1) = b(x1)): f -= (edge coefficient to the boundary)
+ * * b on the unknowns next to that side, so that solving A u = f then imposes u = b there.
+ * Meaningful on a side without PML (see pml_sides).
+ *   side   0: x1 = 0, 1: x1 = 1, 2: x2 = 0, 3: x2 = 1 (the caller's orientation, also for a
+ *          downward handle)
+ *   b      device, [nrhs][n] complex128, the data along the side in node order
+ *   f      device, [nrhs][n*n] complex128, updated in place
+ * Stream-ordered on the handle's stream; HSWEEP_ERR_ARG on a bad side or pointer.
+ */
+HSWEEP_API int hsweep_boundary_rhs(hsweep_t h, int side, const hsw_c128* b, hsw_c128* f, int nrhs);
 
 /* Last device-side error code (an HSWEEP_ERR_* value, 0 if none) and the layer
    (0-based row m) where it was raised, or -1.  Synchronises. */

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_
                 -5: "ERR_NOT_CONVERGED", -6: "ERR_TIMEOUT"}
 
 EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_apply", "hsweep_matvec",
+            "hsweep_boundary_rhs",
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
             "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan"]
@@ -34,7 +35,7 @@ class hsweep_opts(ctypes.Structure):
                 ("pml_C", ctypes.c_double), ("pml_form", ctypes.c_int), ("gmres_max_it", ctypes.c_int),
                 ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int),
                 ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int),
-                ("sweep_dir", ctypes.c_int)]
+                ("sweep_dir", ctypes.c_int), ("pml_sides", ctypes.c_int)]
 
 
 class HSweepError(RuntimeError):
@@ -55,6 +56,7 @@ def load_library(path=LIB_PATH):
         "hsweep_create": (I, [P, D, I, I, D, ctypes.POINTER(hsweep_opts), P, ctypes.POINTER(P)]),
         "hsweep_apply": (I, [P, P, P, I]),
         "hsweep_matvec": (I, [P, P, P, I]),
+        "hsweep_boundary_rhs": (I, [P, I, P, P, I]),
         "hsweep_solve": (I, [P, P, P, I, D, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "hsweep_grad": (I, [P, P, I, P, I, P, P, ctypes.POINTER(D), D]),
         "hsweep_status": (I, [P, ctypes.POINTER(I)]),
@@ -180,6 +182,16 @@ class Handle:
         _check(_lib.hsweep_matvec(self.raw, _ptr(x2, torch.complex128), _ptr(y, torch.complex128),
                                   x2.shape[0]), "hsweep_matvec")
         return y.reshape(x.shape)
+
+    def boundary_rhs(self, side, b, f):
+        """f -= (edge coefficient) * b on the unknowns next to `side` (0: x1 = 0, 1: x1 = 1,
+        2: x2 = 0, 3: x2 = 1): Dirichlet data b ((nrhs, n) complex128) moved into f
+        ((nrhs, n*n) complex128, updated in place; Section 2.5)."""
+        f2 = f.reshape(-1, self.N)
+        b2 = b.reshape(f2.shape[0], -1).contiguous()
+        _check(_lib.hsweep_boundary_rhs(self.raw, int(side), _ptr(b2, torch.complex128), _ptr(f2, torch.complex128),
+                                        f2.shape[0]), "hsweep_boundary_rhs")
+        return f
 
     def solve(self, f, tol, u=None, check=True):
         """GMRES on M A u = M f; returns (u, iterations per RHS, true relative residuals)."""

@@ -52,6 +52,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->sweep_kernel = 0;
   o->sweep_tc = 0;
   o->sweep_dir = 1;
+  o->pml_sides = 15;
   return HSWEEP_OK;
 }
 
@@ -87,7 +88,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
       opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
       opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
-      (opt.sweep_dir != 1 && opt.sweep_dir != -1))
+      (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15)
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -163,7 +164,12 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
     for (size_t i = 0; i < N; ++i)
       if (!(hc[i] > 0) || !std::isfinite(hc[i])) { destroy(h); return HSWEEP_ERR_ARG; }
   }
-  TRY(hsw_assemble(h, opt.pml_C, opt.pml_form));
+  {
+    // the reflected problem of a downward sweep swaps the layers at x2 = 0 and x2 = 1
+    int sides = opt.pml_sides;
+    if (h->dir < 0) sides = (sides & 3) | ((sides & 4) << 1) | ((sides & 8) >> 1);
+    TRY(hsw_assemble(h, opt.pml_C, opt.pml_form, sides));
+  }
   TRYC(cudaStreamSynchronize(h->stream));
 #undef TRY
 #undef TRYC
@@ -179,6 +185,15 @@ extern "C" int hsweep_create(const double* c_dev, double omega, int n, int pml_w
 extern "C" int hsweep_setup(const double* c_dev, double omega, int n, int pml_width, double eps_H,
                             const hsweep_opts* opt, void* stream, hsweep_t* out) {
   if (!out) return HSWEEP_ERR_ARG;
+  {
+    // the sweep must start at a side with a PML: next to a Dirichlet side the first
+    // Schur complements have no absorption and the factorisation is not reliable
+    hsweep_opts o;
+    hsweep_default_opts(&o);
+    if (opt) o = *opt;
+    const int start_bit = o.sweep_dir < 0 ? 8 : 4;
+    if (pml_width > 0 && (o.pml_sides & start_bit) == 0) return HSWEEP_ERR_ARG;
+  }
   hsweep_t h = nullptr;
   int rc = create_impl(c_dev, omega, n, pml_width, eps_H, opt, stream, &h);
   if (rc != HSWEEP_OK) return rc;
@@ -276,6 +291,11 @@ extern "C" int hsweep_grad(hsweep_t h, const hsw_c128* f, int nsrc, const int* r
   if ((rc = hsw_flip_real(h, ga, grad))) return rc;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HSWEEP_ERR_CUDA;
   return HSWEEP_OK;
+}
+
+extern "C" int hsweep_boundary_rhs(hsweep_t h, int side, const hsw_c128* b, hsw_c128* f, int nrhs) {
+  if (!h || side < 0 || side > 3 || nrhs < 0 || (nrhs > 0 && (!b || !f))) return HSWEEP_ERR_ARG;
+  return hsw_boundary_rhs(h, side, reinterpret_cast<const c128*>(b), reinterpret_cast<c128*>(f), nrhs);
 }
 
 extern "C" int hsweep_status(hsweep_t h, int* layer_out) {

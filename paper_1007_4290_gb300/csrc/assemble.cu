@@ -4,12 +4,13 @@
 
 namespace {
 
-// s(t) = 1 / (1 + i sigma(t)/omega), sigma of Eq. sigma.
-__device__ c128 stretch(double t, double eta, double pref, double omega) {
+// s(t) = 1 / (1 + i sigma(t)/omega), sigma of Eq. sigma; lo / hi: the layer at t = 0 /
+// t = 1 is present (a side without it is a plain Dirichlet boundary, Section 2.5)
+__device__ c128 stretch(double t, double eta, double pref, double omega, bool lo, bool hi) {
   double sig = 0.0;
   if (eta > 0.0) {
-    if (t < eta) { double q = (t - eta) / eta; sig = pref * q * q; }
-    else if (t > 1.0 - eta) { double q = (t - 1.0 + eta) / eta; sig = pref * q * q; }
+    if (t < eta) { if (lo) { double q = (t - eta) / eta; sig = pref * q * q; } }
+    else if (t > 1.0 - eta) { if (hi) { double q = (t - 1.0 + eta) / eta; sig = pref * q * q; } }
   }
   return cinv(c128(1.0, sig / omega));
 }
@@ -17,19 +18,20 @@ __device__ c128 stretch(double t, double eta, double pref, double omega) {
 // One thread per node (i, j): the two edge coefficients east[j][i] (edge to the left
 // of node i in row j) and north[j][i] (edge below node i), plus the node terms.  The
 // right/upper boundary edges (index n) are written by the threads of the last column/row.
-__global__ void assemble_kernel(int n, double h, double eta, double pref, double omega,
+__global__ void assemble_kernel(int n, double h, double eta, double pref, double omega, int sides,
                                 const double* __restrict__ c, c128* diag, c128* east,
                                 c128* north, c128* s1s2) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
   if (i >= n || j >= n) return;
   double ih2 = 1.0 / (h * h);
-  c128 si = stretch((i + 1) * h, eta, pref, omega);       // s1 at node i
-  c128 sj = stretch((j + 1) * h, eta, pref, omega);       // s2 at row j
-  c128 sih_l = stretch((i + 0.5) * h, eta, pref, omega);  // half point i - 1/2
-  c128 sih_r = stretch((i + 1.5) * h, eta, pref, omega);  // half point i + 1/2
-  c128 sjh_l = stretch((j + 0.5) * h, eta, pref, omega);
-  c128 sjh_r = stretch((j + 1.5) * h, eta, pref, omega);
+  const bool l1 = sides & 1, h1 = sides & 2, l2 = sides & 4, h2 = sides & 8;
+  c128 si = stretch((i + 1) * h, eta, pref, omega, l1, h1);       // s1 at node i
+  c128 sj = stretch((j + 1) * h, eta, pref, omega, l2, h2);       // s2 at row j
+  c128 sih_l = stretch((i + 0.5) * h, eta, pref, omega, l1, h1);  // half point i - 1/2
+  c128 sih_r = stretch((i + 1.5) * h, eta, pref, omega, l1, h1);  // half point i + 1/2
+  c128 sjh_l = stretch((j + 0.5) * h, eta, pref, omega, l2, h2);
+  c128 sjh_r = stretch((j + 1.5) * h, eta, pref, omega, l2, h2);
   c128 inv_sj = cinv(sj), inv_si = cinv(si);
   c128 e_l = ih2 * (sih_l * inv_sj), e_r = ih2 * (sih_r * inv_sj);   // (s1/s2)_{i -+ 1/2, j}/h^2
   c128 n_l = ih2 * (sjh_l * inv_si), n_r = ih2 * (sjh_r * inv_si);   // (s2/s1)_{i, j -+ 1/2}/h^2
@@ -109,11 +111,11 @@ __global__ void matvec_kernel(int n, long long N, int nrhs, const c128* __restri
 
 }  // namespace
 
-int hsw_assemble(hsweep_s* h, double pml_C, int pml_form) {
+int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides) {
   double eta = h->pml_width * h->h;
   double pref = (pml_form == 0 && eta > 0) ? pml_C / eta : pml_C;
   dim3 grid(div_up(h->n, 128), h->n);
-  assemble_kernel<<<grid, 128, 0, h->stream>>>(h->n, h->h, eta, pref, h->omega, h->d_c,
+  assemble_kernel<<<grid, 128, 0, h->stream>>>(h->n, h->h, eta, pref, h->omega, pml_sides, h->d_c,
                                                 h->d_diag, h->d_east, h->d_north, h->d_s1s2);
   h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
@@ -135,3 +137,38 @@ int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp) {
 }
 
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs) { return hsw_matvec_prec(h, x, y, nrhs, false); }
+
+namespace {
+
+// f[s][node next to the side, k] -= (edge coefficient to the boundary) * b[s][k]
+__global__ void boundary_rhs_kernel(int n, long long N, int nrhs, int side, int dir, const c128* __restrict__ east,
+                                    const c128* __restrict__ north, const c128* __restrict__ b,
+                                    c128* __restrict__ f) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)nrhs * n) return;
+  const int s = (int)(e / n), k = (int)(e - (long long)s * n);
+  const int jint = dir > 0 ? k : n - 1 - k;     // handle row of caller row k
+  long long p;
+  c128 coef;
+  switch (side) {
+    case 0: p = (long long)k * n; coef = east[(long long)jint * (n + 1)]; break;
+    case 1: p = (long long)k * n + n - 1; coef = east[(long long)jint * (n + 1) + n]; break;
+    case 2: p = k; coef = north[(long long)(dir > 0 ? 0 : n) * n + k]; break;
+    default: p = (long long)(n - 1) * n + k; coef = north[(long long)(dir > 0 ? n : 0) * n + k]; break;
+  }
+  c128 v = f[(long long)s * N + p];
+  cfma(v, -coef, b[(long long)s * n + k]);
+  f[(long long)s * N + p] = v;
+}
+
+}  // namespace
+
+int hsw_boundary_rhs(hsweep_s* h, int side, const c128* b, c128* f, int nrhs) {
+  if (nrhs <= 0) return HSWEEP_OK;
+  const long long work = (long long)nrhs * h->n;
+  boundary_rhs_kernel<<<div_up(work, 256), 256, 0, h->stream>>>(h->n, (long long)h->N, nrhs, side, h->dir, h->d_east,
+                                                                h->d_north, b, f);
+  h->nlaunch += 1;
+  HSW_CUDA(cudaGetLastError());
+  return HSWEEP_OK;
+}

@@ -110,7 +110,9 @@ int hsw_alloc(hsweep_s* h, void** p, size_t bytes);
 void hsw_release(hsweep_s* h, void* p);
 
 // assemble.cu
-int hsw_assemble(hsweep_s* h, double pml_C, int pml_form);
+int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides);
+// Dirichlet data b on one side as a forcing term on the adjacent layer (Section 2.5)
+int hsw_boundary_rhs(hsweep_s* h, int side, const c128* b, c128* f, int nrhs);
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
 // the same product with FP32 arithmetic (lowp) on the FP64 vectors
 int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp);

@@ -72,6 +72,25 @@ def velocity_linear_x2(n, c0=0.5, slope=1.0):
     return np.tile((c0 + slope * x)[:, None], (1, n))
 
 
+def velocity_waveguide(n):
+    """A vertical waveguide with a Gaussian cross section: c = (4/3)(1 - 0.5 exp(-32 (x1 - 1/2)^2)),
+    constant along x2 (the same profile as velocity_lens, in x1 only)."""
+    x, _ = grid(n)
+    row = (4.0 / 3.0) * (1.0 - 0.5 * np.exp(-32.0 * (x - 0.5) ** 2))
+    return np.tile(row[None, :], (n, 1))
+
+
+def source_wavepacket(n, center, direction, k, sigma):
+    """Gaussian wave packet exp(-|x - x0|^2 / (2 sigma^2)) exp(i k d.(x - x0)), d the unit
+    vector along `direction` (complex128)."""
+    x, _ = grid(n)
+    X1, X2 = np.meshgrid(x, x, indexing="xy")
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    r1, r2 = X1 - center[0], X2 - center[1]
+    return np.exp(-(r1 * r1 + r2 * r2) / (2.0 * sigma * sigma) + 1j * k * (d[0] * r1 + d[1] * r2))
+
+
 def source_gaussian(n, center=(0.5, 0.5), sigma=1.0 / 64.0):
     """Unnormalised Gaussian f = exp(-|x - x0|^2 / (2 sigma^2)) (complex128)."""
     x, _ = grid(n)
@@ -145,4 +164,26 @@ def workload(name):
         n = int(name[len("dir_n"):])
         return dict(name=name, n=n, omega=two_pi * (n + 1) / 8.0, pml=8, eps_H=0.0, r_max=2, tol=1e-3,
                     c=velocity_linear_x2(n), f=source_gaussian(n, (0.125, 0.5))[None])
+    if name.startswith(("depth1_n", "depth2_n", "mixed1_n", "mixed2_n")):
+        # Section 3.2, other boundary conditions; q = 8, fixed rank R = 2, tol 1e-3, PML of
+        # one wavelength (8 cells) on the sides in `pml_sides` (1: x1 = 0, 2: x1 = 1,
+        # 4: x2 = 0, 8: x2 = 1), zero Dirichlet on the others.
+        #   depth1/depth2: waveguide, Dirichlet data b on x2 = 1 (b = 1, resp. the slant wave
+        #     exp(i omega x1 / 2)), f = 0 otherwise (the data enters through `b_top`);
+        #   mixed1: c = 1, Dirichlet at x1 = 0 and x1 = 1, packet at (0.5, 0.125) towards
+        #     (cos pi/8, sin pi/8); mixed2: c = 1, Dirichlet at x1 = 1 and x2 = 1, packet at
+        #     (0.5, 0.125) towards (1, 1).
+        kind, n = name.split("_n")
+        n = int(n)
+        omega = two_pi * (n + 1) / 8.0
+        x, _ = grid(n)
+        base = dict(name=name, n=n, omega=omega, pml=8, eps_H=0.0, r_max=2, tol=1e-3)
+        if kind in ("depth1", "depth2"):
+            b = np.ones(n, np.complex128) if kind == "depth1" else np.exp(1j * omega * x / 2.0)
+            return dict(base, pml_sides=1 | 2 | 4, c=velocity_waveguide(n), f=np.zeros((1, n, n), np.complex128),
+                        b_top=b[None, :])
+        direction = (np.cos(np.pi / 8), np.sin(np.pi / 8)) if kind == "mixed1" else (1.0, 1.0)
+        sides = (4 | 8) if kind == "mixed1" else (1 | 4)
+        f = source_wavepacket(n, (0.5, 0.125), direction, omega, 1.0 / 16.0)
+        return dict(base, pml_sides=sides, c=velocity_constant(n), f=f[None])
     raise KeyError(name)
