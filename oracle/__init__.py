@@ -10,6 +10,8 @@ Modules
   direct       O2: direct solves of A u = f (banded LU, sparse LU)
   sweep_exact  O3: exact sweeping factorisation, Algorithms 2.1 / 2.2
   hmatrix      O4: weakly admissible H-matrix algebra (Section 2.3)
+  hmatrix_strong O4s: strongly admissible H-matrix algebra with the randomized SVD
+               for F = H . H (Section 2.3, the strongly admissible case)
   sweep_h      O4: approximate sweeping factorisation, Algorithms 2.5 / 2.6
   gmres        left-preconditioned GMRES on M A u = M f (Section 2.4)
   adjoint      misfit and its adjoint gradient with respect to c(x)

@@ -12,6 +12,7 @@ The middle-loop product equals the forward-loop one (u_m is unchanged in
 between), so it is evaluated once (the remark after Algorithm 2.2).
 """
 import numpy as np
+from . import hmatrix_strong as hs
 from .hmatrix import HMatrix, Trunc, hinv, hsub, tree_depth
 
 
@@ -40,14 +41,22 @@ def tridiag_H(diag, off, lo, depth, L):
 
 
 class HSweep:
-    """The approximate sweeping factorisation {T~_m} of A (Algorithm 2.5)."""
+    """The approximate sweeping factorisation {T~_m} of A (Algorithm 2.5).
 
-    def __init__(self, disc, eps, leaf=8, rmax=None):
+    admissibility "weak" (oracle.hmatrix) or "strong" (oracle.hmatrix_strong, whose
+    F = H . H products draw Gaussian test vectors from numpy's generator seeded with
+    `seed`)."""
+
+    def __init__(self, disc, eps, leaf=8, rmax=None, admissibility="weak", seed=0):
         self.disc = disc
         self.tr = Trunc(eps, rmax)
         n = disc.n
         self.L = tree_depth(n, leaf)
         self.T = []
+        if admissibility == "strong":
+            self._setup_strong(leaf, seed)
+            return
+        assert admissibility == "weak"
         for m in range(n):
             Amm = tridiag_H(disc.diag[m], disc.east[m, 1:-1], 0, 0, self.L)
             if m == 0:
@@ -56,6 +65,18 @@ class HSweep:
                 D = disc.A_off(m)          # A_{m,m-1} = A_{m-1,m}
                 S = hsub(Amm, self.T[m - 1].diagmul(dl=D, dr=D), self.tr)
             self.T.append(hinv(S, self.tr))
+
+    def _setup_strong(self, leaf, seed):
+        """Algorithm 2.5 with strongly admissible H-matrices."""
+        disc, n = self.disc, self.disc.n
+        ct = hs.Clusters(n, leaf)
+        rng = np.random.default_rng(seed)
+        for m in range(n):
+            S = hs.tridiag(ct, disc.diag[m], disc.east[m, 1:-1])
+            if m > 0:
+                D = disc.A_off(m)
+                S = hs.hsub(S, self.T[m - 1].root.diagmul(D, D), self.tr)
+            self.T.append(hs.StrongH(hs.hinv(S, self.tr, rng)))
 
     def apply(self, f):
         """Algorithm 2.6: u = M f.  f: (N,) or (N, k)."""
