@@ -244,6 +244,9 @@ def main():
     ap.add_argument("--direction-table", default="",
                     help="comma-separated n (e.g. 127,255,511): GMRES steps and times of the upward and "
                          "downward sweeps on the sweeping-direction workload (Section 3.1), one JSON line")
+    ap.add_argument("--strong-rank", type=int, default=0,
+                    help="with --direction-table / --boundary-table: strongly admissible H-matrices of "
+                         "rank R (Section 2.3; Section 3 uses R = 2) instead of weak ones of rank 2")
     args = ap.parse_args()
 
     if args.cpu_sample is not None:
@@ -429,6 +432,23 @@ def main():
         dist.destroy_process_group()
 
 
+def _rank_opts(args, w):
+    """Options of the paper-protocol tables: FP64 with R = 2 on the weakly admissible blocks,
+    or with --strong-rank R the strongly admissible case (the configuration of Section 3),
+    in mixed precision: its weak inverse runs at the default rank cap with eps_H = 1e-6
+    before the rank-R projection (FP64 at that cap would take minutes per setup at n = 1023)."""
+    import paper_1007_4290_gb300 as hs
+    if args.strong_rank > 0:
+        return {"strong_rank": args.strong_rank, "precision": hs.MIXED}, 1e-6
+    return {"r_max": w["r_max"], "precision": hs.FP64}, w["eps_H"]
+
+
+def _rank_label(args):
+    if args.strong_rank > 0:
+        return "mixed precision, strong admissibility, R = %d" % args.strong_rank
+    return "FP64, weak admissibility, R = 2"
+
+
 def run_direction_table(args):
     """The sweeping-direction test of Section 3.1 (c = 1/2 + x2, point source at
     (0.125, 0.5), q = 8, fixed rank R = 2, GMRES tolerance 1e-3, FP64): setup and solve
@@ -441,10 +461,11 @@ def run_direction_table(args):
         f = torch.tensor(w["f"].reshape(1, -1), device="cuda")
         row = {"n": n, "omega_over_2pi": w["omega"] / (2 * np.pi), "R": w["r_max"]}
         for direction, key in ((1, "up"), (-1, "down")):
-            opts = hs.default_opts(precision=hs.FP64, r_max=w["r_max"], sweep_dir=direction)
+            kw, eps = _rank_opts(args, w)
+            opts = hs.default_opts(sweep_dir=direction, **kw)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], w["eps_H"], opts)
+            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], eps, opts)
             torch.cuda.synchronize()
             t_setup = time.perf_counter() - t0
             u = torch.zeros_like(f)
@@ -457,8 +478,8 @@ def run_direction_table(args):
             row[key] = {"setup_s": t_setup, "solve_s": time.perf_counter() - t0, "iters": it[0], "relres": rr[0]}
             h.free()
         rows.append(row)
-    print(json.dumps({"metric": "GMRES steps, sweeping-direction test (Section 3.1), FP64, R = 2, tol 1e-3",
-                      "data": "synthetic", "rows": rows}))
+    print(json.dumps({"metric": "GMRES steps, sweeping-direction test (Section 3.1), %s, tol 1e-3"
+                                % _rank_label(args), "data": "synthetic", "rows": rows}))
 
 
 def run_boundary_table(args):
@@ -473,10 +494,11 @@ def run_boundary_table(args):
         row = {"n": n}
         for kind in ("depth1", "depth2", "mixed1", "mixed2"):
             w = synth.workload("%s_n%d" % (kind, n))
-            opts = hs.default_opts(precision=hs.FP64, r_max=w["r_max"], pml_sides=w["pml_sides"])
+            kw, eps = _rank_opts(args, w)
+            opts = hs.default_opts(pml_sides=w["pml_sides"], **kw)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], w["eps_H"], opts)
+            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], eps, opts)
             torch.cuda.synchronize()
             t_setup = time.perf_counter() - t0
             f0 = torch.tensor(w["f"].reshape(1, -1), device="cuda")
@@ -492,8 +514,8 @@ def run_boundary_table(args):
             row[kind] = {"setup_s": t_setup, "solve_s": time.perf_counter() - t0, "iters": it[0], "relres": rr[0]}
             h.free()
         rows.append(row)
-    print(json.dumps({"metric": "GMRES steps, boundary-condition examples (Section 3.2), FP64, R = 2, tol 1e-3",
-                      "data": "synthetic", "rows": rows}))
+    print(json.dumps({"metric": "GMRES steps, boundary-condition examples (Section 3.2), %s, tol 1e-3"
+                                % _rank_label(args), "data": "synthetic", "rows": rows}))
 
 
 def run_parts(args):

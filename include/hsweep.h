@@ -6,7 +6,8 @@
  * equation: hierarchical matrix representation" (2010).
  *   - Section 2.1, Eq. sigma / Eq. helmd: PML stretching and the 5-point matrix A.
  *   - Algorithm 2.5: setup sweep S~_m = A_mm - A_{m,m-1} T~_{m-1} A_{m-1,m},
- *     T~_m = hinv(S~_m), every T~_m held as a weakly admissible H-matrix (Section 2.3).
+ *     T~_m = hinv(S~_m), every T~_m held as a weakly admissible H-matrix (Section 2.3),
+ *     or in the strongly admissible case with rank R (hsweep_opts.strong_rank).
  *   - Algorithm 2.6: the apply u = M f (forward and backward sweeps of hmatvec).
  *   - Section 2.4: GMRES on M A u = M f.
  *
@@ -28,6 +29,8 @@
  */
 #ifndef HSWEEP_H
 #define HSWEEP_H
+
+#include <stdint.h>
 
 #if defined(__GNUC__)
 #define HSWEEP_API __attribute__((visibility("default")))
@@ -97,10 +100,32 @@ typedef struct {
                         next to a Dirichlet side the first Schur complements have no
                         absorption (a downward sweep of the depth-extrapolation problem met
                         the GMRES test with a wrong solution in testing) */
+  int strong_rank;   /* 0 (default): weakly admissible H-matrices (siblings are each other's
+                        interaction list; Section 2.3).  R = 1..8: the strongly admissible
+                        case (Section 2.3; the configuration of the experiments of Section 3,
+                        with R = 2): clusters i, i' of one depth are well separated when
+                        |i - i'| >= 2, the blocks of the interaction lists have rank at most R
+                        (eps_H still truncates below R), neighbouring leaves are dense.  Each
+                        T~_m is the rank-R projection, by the randomized SVD with R + 8
+                        Gaussian test vectors, of the weakly admissible inverse of S~_m
+                        (rank cap r_max); it is stored exactly in the sibling-pair factor
+                        layout with rank 3 R (L - depth) + leaf at each depth, and r_max is
+                        raised to 3 R (L - 1) + leaf when smaller (HSWEEP_ERR_ARG above 56) */
+  unsigned rsvd_seed; /* key of the Philox4x32-10 generator of those test vectors (default 0) */
 } hsweep_opts;
 
 /* Fill *o with the defaults listed above. */
 HSWEEP_API int hsweep_default_opts(hsweep_opts* o);
+
+/*
+ * The counter-based generator of the randomized SVD's test vectors: Philox4x32-10 (Salmon,
+ * Moraes, Dror and Shaw, SC 2011) of the 128-bit counter ctr[4] under the 64-bit key key[2],
+ * written to out[4] (host pointers; host computation, no device needed).  The device draws
+ * a complex normal pair from the block with counter {row, column pair, block, layer} and
+ * key {rsvd_seed, 0x5EED} by the Box-Muller transform.
+ * Returns HSWEEP_ERR_ARG on a NULL pointer.
+ */
+HSWEEP_API int hsweep_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
 /*
  * Assemble A for velocity c at angular frequency omega (Eq. sigma, Eq. helmd; PML of

@@ -26,7 +26,7 @@ EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_appl
             "hsweep_boundary_rhs",
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
-            "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan"]
+            "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan", "hsweep_philox4x32_10"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -35,7 +35,8 @@ class hsweep_opts(ctypes.Structure):
                 ("pml_C", ctypes.c_double), ("pml_form", ctypes.c_int), ("gmres_max_it", ctypes.c_int),
                 ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int),
                 ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int),
-                ("sweep_dir", ctypes.c_int), ("pml_sides", ctypes.c_int)]
+                ("sweep_dir", ctypes.c_int), ("pml_sides", ctypes.c_int),
+                ("strong_rank", ctypes.c_int), ("rsvd_seed", ctypes.c_uint)]
 
 
 class HSweepError(RuntimeError):
@@ -69,6 +70,8 @@ def load_library(path=LIB_PATH):
         "hsweep_stats": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]),
         "hsweep_apply_noalloc": (I, [P, P, P, I]),
         "hsweep_sweep_plan": (I, [P, I, ctypes.POINTER(LL)]),
+        "hsweep_philox4x32_10": (I, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                     ctypes.POINTER(ctypes.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -104,6 +107,16 @@ def default_opts(**kw):
         if v is not None:
             setattr(o, k, v)
     return o
+
+
+def philox4x32_10(ctr, key):
+    """The library's Philox4x32-10 block (hsweep_philox4x32_10) of four 32-bit counter words
+    under two key words, as a list of four ints; host only."""
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    out = (ctypes.c_uint32 * 4)()
+    _check(_lib.hsweep_philox4x32_10(c, k, out), "hsweep_philox4x32_10")
+    return list(out)
 
 
 class Handle:

@@ -1,5 +1,6 @@
 // The C-ABI of include/hsweep.h: argument checks, handle lifetime, factor-store
 // layout, and host<->device copies of single layers.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -53,12 +54,15 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->sweep_tc = 0;
   o->sweep_dir = 1;
   o->pml_sides = 15;
+  o->strong_rank = 0;
+  o->rsvd_seed = 0;
   return HSWEEP_OK;
 }
 
 static void destroy(hsweep_s* h) {
   if (!h) return;
   hsw_setup_free(h);
+  hsw_strong_free(h);
   hsw_krylov_free(h);
   for (auto& pr : h->ev_sweep) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
@@ -88,7 +92,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
       opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
       opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
-      (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15)
+      (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15 ||
+      opt.strong_rank < 0 || opt.strong_rank > 8)
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -106,6 +111,13 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
   h->nnodes = h->tree.nnodes;
   h->nleaves = h->tree.nleaves;
   h->r_max = opt.r_max;
+  h->strong_R = opt.strong_rank;
+  if (h->strong_R > 0) {
+    // the expanded strong form needs this rank at depth 1
+    const int need = hsw_strong_expansion_rank(h->strong_R, h->L, h->leaf);
+    if (need > 56) { delete h; return HSWEEP_ERR_ARG; }
+    h->r_max = std::max(h->r_max, need);
+  }
   h->prec = opt.precision;
   h->dir = opt.sweep_dir;
   int rc = HSWEEP_OK;

@@ -29,12 +29,8 @@ struct Tree {
   int maxsz(int d) const { return (n + (1 << d) - 1) >> d; }
 };
 
-struct SetupWork;   // direction.cu: reversal of the layer order (x2 -> 1 - x2)
-int hsw_flip_reserve(hsweep_s* h, size_t bytes);
-int hsw_flip_c128(hsweep_s* h, const c128* in, c128* out, int nvec);
-int hsw_flip_real(hsweep_s* h, const double* in, double* out);
-int hsw_flip_index(hsweep_s* h, const int* in, int* out, int cnt);
-// setup.cu
+struct SetupWork;   // setup.cu
+struct StrongWork;  // strong.cu
 struct KrylovWork;  // krylov.cu
 
 struct hsweep_s {
@@ -92,6 +88,9 @@ struct hsweep_s {
 
   SetupWork* sw = nullptr;
   KrylovWork* kw = nullptr;
+  // strong admissibility (strong.cu): rank R of the well-separated blocks, 0 = weak
+  int strong_R = 0;
+  StrongWork* stw = nullptr;
 
   std::vector<void*> allocs;   // every device allocation owned by the handle
 
@@ -137,6 +136,13 @@ int hsw_flip_reserve(hsweep_s* h, size_t bytes);
 int hsw_flip_c128(hsweep_s* h, const c128* in, c128* out, int nvec);
 int hsw_flip_real(hsweep_s* h, const double* in, double* out);
 int hsw_flip_index(hsweep_s* h, const int* in, int* out, int cnt);
+// strong.cu: rank-R projection of the weak T~_m onto the strongly admissible partition,
+// written back into the factor buffers G_F2 (ranks into G_rank)
+int hsw_strong_project(hsweep_s* h, int m, const void* G_F, int* G_rank, void* G_F2, const long long* d_gfo,
+                       long long gf_entries);
+int hsw_strong_expansion_rank(int R, int L, int leaf);
+void hsw_strong_free(hsweep_s* h);
+__host__ __device__ void hsw_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 // setup.cu
 int hsw_factor(hsweep_s* h);
 void hsw_setup_free(hsweep_s* h);

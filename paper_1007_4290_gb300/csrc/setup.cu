@@ -694,6 +694,7 @@ __global__ void store_layer(Geo g, const Cx<R>* __restrict__ G_leaf, const Cx<R>
 // ---------------------------------------------------------------------------------------
 struct SetupWork {
   int KCAP = 0, WCAP = 0;
+  long long gfo_total = 0;   // entries of one G factor buffer
   std::vector<long long> sfo, gfo;
   std::vector<int> rowleaf;
   long long* d_sfo = nullptr;
@@ -746,6 +747,7 @@ static int setup_alloc(hsweep_s* h) {
   A(w->S_F, std::max(so, 1LL) * es);
   A(w->G_F, std::max(go, 1LL) * es);
   A(w->G_F2, std::max(go, 1LL) * es);
+  w->gfo_total = std::max(go, 1LL);
   A(w->Y, (long long)h->n * w->KCAP * es);
   A(w->W, (long long)h->n * w->KCAP * es);
   A(w->Qr, (long long)nn * h->r_max * w->KCAP * es);
@@ -848,6 +850,11 @@ static int factor_impl(hsweep_s* h) {
       h->nlaunch += 1;
       recompress_apply<R><<<n_below1, kBlk, 0, st>>>(g, d, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);
       h->nlaunch += 1;
+      std::swap(G_F, G_F2);
+    }
+    if (h->strong_R > 0) {
+      int rc = hsw_strong_project(h, m, G_F, w->G_rank, G_F2, w->d_gfo, w->gfo_total);
+      if (rc) return rc;
       std::swap(G_F, G_F2);
     }
     store_layer<R><<<nn, kBlk, 0, st>>>(g, G_leaf, G_F, w->G_rank, fac + (long long)m * h->layer_stride,

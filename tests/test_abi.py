@@ -56,3 +56,28 @@ def test_default_opts_and_argument_checks_without_gpu():
     assert rc == hs.ERR_ARG
     assert hs._lib.hsweep_apply(None, None, None, 1) == hs.ERR_ARG
     hs._lib.hsweep_free(None)
+
+
+def test_philox_generator_matches_the_published_known_answers():
+    # the counter-based generator of the randomized SVD's test vectors (strong admissibility)
+    _lib_path()
+    import paper_1007_4290_gb300 as hs
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert hs.philox4x32_10(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_strong_rank_argument_checks_without_gpu():
+    _lib_path()
+    import paper_1007_4290_gb300 as hs
+    raw = ctypes.c_void_p()
+    for bad in (hs.default_opts(strong_rank=9), hs.default_opts(strong_rank=-1)):
+        rc = hs._lib.hsweep_setup(ctypes.c_void_p(16), 1.0, 64, 8, 1e-6, ctypes.byref(bad), None, ctypes.byref(raw))
+        assert rc == hs.ERR_ARG and not raw.value
+    # n = 2047, leaf 8: depth 8, the expanded strong form of rank 3 needs 3*3*7 + 8 = 71 > 56 columns
+    o = hs.default_opts(strong_rank=3)
+    rc = hs._lib.hsweep_setup(ctypes.c_void_p(16), 1.0, 2047, 16, 1e-6, ctypes.byref(o), None, ctypes.byref(raw))
+    assert rc == hs.ERR_ARG and not raw.value
