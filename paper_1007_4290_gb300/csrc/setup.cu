@@ -853,8 +853,18 @@ static int factor_impl(hsweep_s* h) {
       std::swap(G_F, G_F2);
     }
     if (h->strong_R > 0) {
+      // strongly admissible T~_m (strong.cu), then one recompression of every sibling pair:
+      // the expanded layout can carry more columns than a block has rows (small blocks,
+      // blocks of rank below R); the recompression keeps the same matrix up to eps_H and
+      // brings every rank to at most the block's dimensions, as the sweeps expect
       int rc = hsw_strong_project(h, m, G_F, w->G_rank, G_F2, w->d_gfo, w->gfo_total);
       if (rc) return rc;
+      std::swap(G_F, G_F2);
+      const int n_all = nn - 2;
+      qr_cgs2<R><<<n_all, 1024, qr_smem, st>>>(g, 0, G_F, w->G_rank, Rb, w->qcols);
+      svd_jacobi<R><<<n_all / 2, 1024, svd_smem, st>>>(g, 0, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx, w->newrank);
+      recompress_apply<R><<<n_all, kBlk, 0, st>>>(g, 0, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);
+      h->nlaunch += 3;
       std::swap(G_F, G_F2);
     }
     store_layer<R><<<nn, kBlk, 0, st>>>(g, G_leaf, G_F, w->G_rank, fac + (long long)m * h->layer_stride,

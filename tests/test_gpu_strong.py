@@ -17,6 +17,7 @@ from oracle.gmres import preconditioned_solve
 from oracle.hmatrix_strong import Clusters
 from oracle.sweep_exact import setup_exact, solve_exact
 from oracle.sweep_h import HSweep
+from tests.helpers import layer_to_dense
 
 pytestmark = pytest.mark.gpu
 
@@ -35,10 +36,10 @@ def _small():
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-4)])
 def test_strong_form_with_full_rank_is_the_exact_sweep(hs, prec, tol):
-    # n = 31, leaves of 4: the well-separated blocks are at most 8 x 8, so R = 8 keeps
-    # every singular value and the strong T~_m are the exact T_m
+    # n = 31, leaves of 8 (depth 2): the well-separated blocks are at most 8 x 8, so
+    # R = 8 keeps every singular value and the strong T~_m are the exact T_m
     n, c, omega, pml = _small()
-    opts = hs.default_opts(precision=prec, leaf=4, strong_rank=8)
+    opts = hs.default_opts(precision=prec, leaf=8, strong_rank=8)
     h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 0.0, opts)
     rng = np.random.default_rng(4)
     R = rng.standard_normal((3, n * n)) + 1j * rng.standard_normal((3, n * n))
@@ -52,28 +53,41 @@ def test_strong_form_with_full_rank_is_the_exact_sweep(hs, prec, tol):
         assert np.linalg.norm(Z[s] - ref) / np.linalg.norm(ref) < tol
 
 
-@pytest.mark.parametrize("R", [1, 2, 4])
-def test_layer_ranks_follow_the_expanded_strong_layout(hs, R):
-    # every sibling pair (a, b) at depth l carries 3 R (L - l) columns for the
-    # well-separated blocks below it plus the corner block of neighbouring leaves
-    # (as many columns as the leftmost leaf of b has rows)
+@pytest.mark.parametrize("R", [1, 2])
+def test_well_separated_blocks_of_the_factors_have_rank_at_most_R(hs, R):
+    # the strongly admissible structure of every exported T~_m: each block of an
+    # interaction list has numerical rank at most R, and the stored sibling ranks stay
+    # within 3 R (L - l) + (leaf rows) and within the block dimensions
     w = synth.workload("mixed2_n127")
     n = w["n"]
-    opts = hs.default_opts(precision=1, strong_rank=R)
-    h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], 0.0,
-                        hs.default_opts(precision=1, strong_rank=R, pml_sides=w["pml_sides"]))
-    L = h.info()["L"]
+    opts = hs.default_opts(precision=0, strong_rank=R, pml_sides=w["pml_sides"])
+    h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], 0.0, opts)
+    inf = h.info()
+    L = inf["L"]
     ct = Clusters(n, 8)
     assert ct.L == L
-    exp = [0, 0]
-    for v in range(2, 1 << (L + 1)):
-        l = v.bit_length() - 1
-        b = v | 1
-        leaf_b = (b << (L - l)) - (1 << L)
-        exp.append(3 * R * (L - l) + ct.size(L, leaf_b))
     for m in (0, 1, n // 2, n - 1):
-        assert h.layer_ranks(m) == exp
-    assert h.info()["r_max"] >= 3 * R * (L - 1) + 8
+        lv, fac, rk = h.export_layer(m)
+        for v in range(2, 1 << (L + 1)):
+            l = v.bit_length() - 1
+            b = v | 1
+            leaf_b = (b << (L - l)) - (1 << L)
+            cap = min(3 * R * (L - l) + ct.size(L, leaf_b), ct.size(l, (v & ~1) - (1 << l)),
+                      ct.size(l, b - (1 << l)))
+            assert rk[v] <= cap, (m, v, rk[v], cap)
+        T = layer_to_dense(n, 8, inf["r_max"], lv, fac, rk)
+        tn = np.linalg.norm(T, 2)
+        nblk = 0
+        for l in range(2, L + 1):
+            for i in range(1 << l):
+                for j in ct.interaction_list(l, i):
+                    r0, r1 = ct.range(l, i)
+                    c0, c1 = ct.range(l, j)
+                    sv = np.linalg.svd(T[r0:r1, c0:c1], compute_uv=False)
+                    if sv[0] > 1e-6 * tn and sv.size > R:
+                        assert sv[R] <= 1e-9 * sv[0], (m, l, i, j, sv[:R + 2])
+                        nblk += 1
+        assert nblk > 0
     h.free()
 
 
