@@ -244,8 +244,11 @@ def main():
     ap.add_argument("--direction-table", default="",
                     help="comma-separated n (e.g. 127,255,511): GMRES steps and times of the upward and "
                          "downward sweeps on the sweeping-direction workload (Section 3.1), one JSON line")
+    ap.add_argument("--pml-table", default="",
+                    help="comma-separated n: GMRES steps and times of the PML examples of Section 3.1 "
+                         "(lens, waveguide, random medium; point source and wave packet), one JSON line")
     ap.add_argument("--strong-rank", type=int, default=0,
-                    help="with --direction-table / --boundary-table: strongly admissible H-matrices of "
+                    help="with --direction-table / --boundary-table / --pml-table: strongly admissible H-matrices of "
                          "rank R (Section 2.3; Section 3 uses R = 2) instead of weak ones of rank 2")
     args = ap.parse_args()
 
@@ -262,6 +265,9 @@ def main():
         return
     if args.direction_table:
         run_direction_table(args)
+        return
+    if args.pml_table:
+        run_pml_table(args)
         return
     if args.boundary_table:
         run_boundary_table(args)
@@ -515,6 +521,38 @@ def run_boundary_table(args):
             h.free()
         rows.append(row)
     print(json.dumps({"metric": "GMRES steps, boundary-condition examples (Section 3.2), %s, tol 1e-3"
+                                % _rank_label(args), "data": "synthetic", "rows": rows}))
+
+
+def run_pml_table(args):
+    """The dependence-on-omega tables of Section 3.1 (PML on all sides; the lens, the
+    waveguide and a random medium; a point source and a wave packet; q = 8, R = 2,
+    tol 1e-3): setup time, and GMRES steps and solve time per force, per n."""
+    import torch
+    import paper_1007_4290_gb300 as hs
+    rows = []
+    for n in [int(v) for v in args.pml_table.split(",")]:
+        for kind in ("pml1", "pml2", "pml3"):
+            w = synth.workload("%s_n%d" % (kind, n))
+            kw, eps = _rank_opts(args, w)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], eps, hs.default_opts(**kw))
+            torch.cuda.synchronize()
+            row = {"n": n, "field": kind, "setup_s": time.perf_counter() - t0}
+            for s, key in ((0, "point"), (1, "packet")):
+                f = torch.tensor(w["f"][s].reshape(1, -1), device="cuda")
+                u = torch.zeros_like(f)
+                h.solve(f, w["tol"], u=u, check=False)
+                u.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, it, rr = h.solve(f, w["tol"], u=u, check=False)
+                torch.cuda.synchronize()
+                row[key] = {"iters": it[0], "solve_s": time.perf_counter() - t0, "relres": rr[0]}
+            h.free()
+            rows.append(row)
+    print(json.dumps({"metric": "GMRES steps, PML examples (Section 3.1, dependence on omega), %s, tol 1e-3"
                                 % _rank_label(args), "data": "synthetic", "rows": rows}))
 
 

@@ -80,6 +80,27 @@ def velocity_waveguide(n):
     return np.tile(row[None, :], (n, 1))
 
 
+def velocity_random_modes(n, seed=7, kmax=8, amp=0.2):
+    """A random smooth medium that is the same function of x on every grid (for tables over
+    n): c = 1 + amp * g / gmax, g = sum_{j,k <= kmax} a_jk cos(pi j x1 + p_jk) cos(pi k x2 + q_jk),
+    a_jk ~ N(0, 1) / (1 + j^2 + k^2), phases uniform, gmax = max |g| on the 255 x 255 grid."""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((kmax + 1, kmax + 1))
+    j = np.arange(kmax + 1)
+    a = a / (1.0 + j[:, None] ** 2 + j[None, :] ** 2)
+    ph = rng.uniform(0, 2 * np.pi, (2, kmax + 1, kmax + 1))
+
+    def g_on(m):
+        x, _ = grid(m)
+        g = np.zeros((m, m))
+        for jj in range(kmax + 1):
+            for kk in range(kmax + 1):
+                g += a[jj, kk] * np.cos(np.pi * jj * x[None, :] + ph[0, jj, kk]) * np.cos(np.pi * kk * x[:, None] + ph[1, jj, kk])
+        return g
+
+    return 1.0 + amp * g_on(n) / np.abs(g_on(255)).max()
+
+
 def source_wavepacket(n, center, direction, k, sigma):
     """Gaussian wave packet exp(-|x - x0|^2 / (2 sigma^2)) exp(i k d.(x - x0)), d the unit
     vector along `direction` (complex128)."""
@@ -164,6 +185,19 @@ def workload(name):
         n = int(name[len("dir_n"):])
         return dict(name=name, n=n, omega=two_pi * (n + 1) / 8.0, pml=8, eps_H=0.0, r_max=2, tol=1e-3,
                     c=velocity_linear_x2(n), f=source_gaussian(n, (0.125, 0.5))[None])
+    if name.startswith(("pml1_n", "pml2_n", "pml3_n")):
+        # Section 3.1, dependence on omega: PML on all sides, q = 8 (omega / 2 pi = (n + 1) / 8,
+        # relative to c = 1), fixed rank R = 2, tol 1e-3; velocity 1: the converging lens,
+        # 2: the vertical waveguide, 3: a random smooth medium (the same function for every
+        # n); two forces: a narrow Gaussian at (0.5, 0.125) and a Gaussian wave packet at
+        # (0.125, 0.125) towards (1, 1) with the wavelength of c = 1
+        kind, n = name.split("_n")
+        n = int(n)
+        omega = two_pi * (n + 1) / 8.0
+        c = {"pml1": velocity_lens, "pml2": velocity_waveguide, "pml3": velocity_random_modes}[kind](n)
+        f = np.stack([source_gaussian(n, (0.5, 0.125)),
+                      source_wavepacket(n, (0.125, 0.125), (1.0, 1.0), omega, 1.0 / 16.0)])
+        return dict(name=name, n=n, omega=omega, pml=8, eps_H=0.0, r_max=2, tol=1e-3, c=c, f=f)
     if name.startswith(("depth1_n", "depth2_n", "mixed1_n", "mixed2_n")):
         # Section 3.2, other boundary conditions; q = 8, fixed rank R = 2, tol 1e-3, PML of
         # one wavelength (8 cells) on the sides in `pml_sides` (1: x1 = 0, 2: x1 = 1,
