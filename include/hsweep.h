@@ -128,6 +128,32 @@ HSWEEP_API int hsweep_default_opts(hsweep_opts* o);
 HSWEEP_API int hsweep_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
 /*
+ * The Gaussian test vectors of one well-separated block, as the device draws them (host
+ * computation, no device needed): rows x P complex values (P even) column-major in out
+ * (host, 2 * rows * P doubles: re, im), entry (row, p) a complex standard normal from the
+ * Philox block {row, p / 2, blk, m} under key {seed, 0x5EED} by the Box-Muller transform
+ * (the device's sin/cos may differ in the last bits).  Returns HSWEEP_ERR_ARG on bad sizes.
+ */
+HSWEEP_API int hsweep_rsvd_normals(uint32_t blk, uint32_t m, uint32_t seed, int rows, int P, double* out);
+
+/*
+ * The strongly admissible layout of one layer (host computation, no device needed) for n
+ * points, leaves of at most `leaf` (2..8) and rank R (1..8); *nfar, *nnear receive the record
+ * counts; far ([*nfar][8] ints), near ([*nnear][6] ints) and ranks ([2^(L+1)] ints) are
+ * filled when non-NULL (host memory owned by the caller; call once with NULL to size them).
+ *   far:  {a, b, ru0, rw0, su, sw, col, l}: the well-separated block of depth l whose rows are
+ *         rows ru0 .. ru0+su-1 of node a and whose columns are rows rw0 .. rw0+sw-1 of its
+ *         sibling b (heap node numbers, root 1); its rank-R factors occupy columns
+ *         col .. col+R-1 of the expanded F_a, F_b
+ *   near: {a, b, ca0, na, nb, col}: the dense block of the neighbouring leaves at the corner of
+ *         (a, b) (rows ca0 .. ca0+na-1 of a against the first nb rows of b), stored as the
+ *         columns [D | I] from col on
+ *   ranks: the expanded rank of every node (3 R (L - depth) + nb of its pair; 0 for nodes 0, 1)
+ * Returns HSWEEP_ERR_ARG on bad sizes or NULL count pointers.
+ */
+HSWEEP_API int hsweep_strong_plan(int n, int leaf, int R, int* nfar, int* nnear, int* far, int* near, int* ranks);
+
+/*
  * Assemble A for velocity c at angular frequency omega (Eq. sigma, Eq. helmd; PML of
  * width eta = pml_width * h on all four sides) and run the setup sweep of
  * Algorithm 2.5: for m = 1..n, S~_m from T~_{m-1} (hdiagmul + hsub), T~_m = hinv(S~_m).

@@ -26,7 +26,8 @@ EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_appl
             "hsweep_boundary_rhs",
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
-            "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan", "hsweep_philox4x32_10"]
+            "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan", "hsweep_philox4x32_10",
+            "hsweep_rsvd_normals", "hsweep_strong_plan"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -72,6 +73,8 @@ def load_library(path=LIB_PATH):
         "hsweep_sweep_plan": (I, [P, I, ctypes.POINTER(LL)]),
         "hsweep_philox4x32_10": (I, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                      ctypes.POINTER(ctypes.c_uint32)]),
+        "hsweep_rsvd_normals": (I, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, I, I, P]),
+        "hsweep_strong_plan": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -117,6 +120,34 @@ def philox4x32_10(ctr, key):
     out = (ctypes.c_uint32 * 4)()
     _check(_lib.hsweep_philox4x32_10(c, k, out), "hsweep_philox4x32_10")
     return list(out)
+
+
+def rsvd_normals(blk, m, seed, rows, P):
+    """hsweep_rsvd_normals: the (rows, P) complex Gaussian test vectors of block `blk` of
+    layer m (host only)."""
+    import numpy as np
+    out = np.zeros(2 * rows * P, np.float64)
+    _check(_lib.hsweep_rsvd_normals(blk, m, seed, rows, P, out.ctypes.data_as(ctypes.c_void_p)),
+           "hsweep_rsvd_normals")
+    return out.view(np.complex128).reshape(P, rows).T
+
+
+def strong_plan(n, leaf, R):
+    """hsweep_strong_plan: (far (nfar, 8), near (nnear, 6), ranks) int arrays (host only)."""
+    import numpy as np
+    nf, nn = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.hsweep_strong_plan(n, leaf, R, ctypes.byref(nf), ctypes.byref(nn), None, None, None),
+           "hsweep_strong_plan")
+    L = 0
+    while -(-n // (1 << L)) > leaf:
+        L += 1
+    far = np.zeros((max(1, nf.value), 8), np.int32)
+    near = np.zeros((max(1, nn.value), 6), np.int32)
+    ranks = np.zeros(1 << (L + 1), np.int32)
+    _check(_lib.hsweep_strong_plan(n, leaf, R, ctypes.byref(nf), ctypes.byref(nn),
+                                   far.ctypes.data_as(ctypes.c_void_p), near.ctypes.data_as(ctypes.c_void_p),
+                                   ranks.ctypes.data_as(ctypes.c_void_p)), "hsweep_strong_plan")
+    return far[:nf.value], near[:nn.value], ranks
 
 
 class Handle:

@@ -23,6 +23,7 @@
 // The next layer's S~_{m+1} and the sweeps read the expanded store, so both use the
 // strongly admissible T~_m exactly.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 #include "handle.h"
 
@@ -81,7 +82,7 @@ __device__ inline void gauss2(uint32_t row, uint32_t pair, uint32_t blk, uint32_
 struct FarArgs {
   int nblk, R, P;
   uint32_t seed;
-  const int* info;          // [nblk][8]: a, b, ru0, rw0, su, sw, col, (unused)
+  const int* info;          // [nblk][8]: a, b, ru0, rw0, su, sw, col, depth of (u, w)
   const long long* soff;    // [nblk] scratch offset (entries): Omega/Bt (sw x P), then Y/Q (su x P)
   const long long* gfo;     // factor offsets per node
   const int* sz;            // node sizes
@@ -363,19 +364,17 @@ struct StrongWork {
 
 int hsw_strong_expansion_rank(int R, int L, int leaf) { return 3 * R * (L > 0 ? L - 1 : 0) + leaf; }
 
-static int strong_prepare(hsweep_s* h, size_t es) {
-  StrongWork* s = new (std::nothrow) StrongWork();
-  if (!s) return HSWEEP_ERR_OOM;
-  h->stw = s;
-  const Tree& t = h->tree;
-  const int L = h->L, R = h->strong_R;
-  s->P = std::min(kPMax, (R + kOversample + 1) / 2 * 2);
-  std::vector<int> far, near;
-  std::vector<long long> soff;
-  std::vector<int> nrank(h->nnodes, 0);
-  long long so = 0;
+// The strong layout of one layer: far records {a, b, ru0, rw0, su, sw, col, l} (the block
+// (u, w) of depth l inside the sibling pair (a, b), rows ru0.. of a and rw0.. of b, columns
+// col..col+R of the expanded factors), near records {a, b, ca0, na, nb, col} (the corner
+// leaves), and the expanded rank of every node.
+static void strong_plan(const Tree& t, int R, std::vector<int>& far, std::vector<int>& near,
+                        std::vector<int>& nrank) {
+  const int L = t.L;
+  far.clear(); near.clear();
+  nrank.assign(t.nnodes, 0);
   // the sibling pairs (a, b) and, inside each, the corner chain down to the leaves
-  for (int av = 2; av < h->nnodes; av += 2) {
+  for (int av = 2; av < t.nnodes; av += 2) {
     const int bv = av + 1, la = depth_of_host(av);
     int ca = av, cb = bv;      // corner pair at depth l - 1
     for (int l = la + 1; l <= L; ++l) {
@@ -384,10 +383,8 @@ static int strong_prepare(hsweep_s* h, size_t es) {
       for (int tt = 0; tt < 3; ++tt) {
         const int u = us[tt], w = ws[tt];
         const int rec[8] = {av, bv, t.lo[u] - t.lo[av], t.lo[w] - t.lo[bv], t.sz[u], t.sz[w],
-                            R * (3 * (l - la - 1) + tt), 0};
+                            R * (3 * (l - la - 1) + tt), l};
         far.insert(far.end(), rec, rec + 8);
-        soff.push_back(so);
-        so += (long long)(t.sz[u] + t.sz[w]) * s->P;
       }
       ca = 2 * ca + 1;
       cb = 2 * cb;
@@ -397,7 +394,24 @@ static int strong_prepare(hsweep_s* h, size_t es) {
     const int rec[6] = {av, bv, t.lo[ca] - t.lo[av], t.sz[ca], t.sz[cb], col};
     near.insert(near.end(), rec, rec + 6);
     nrank[av] = nrank[bv] = col + t.sz[cb];
-    if (nrank[av] > h->r_max) return HSWEEP_ERR_ARG;
+  }
+}
+
+static int strong_prepare(hsweep_s* h, size_t es) {
+  StrongWork* s = new (std::nothrow) StrongWork();
+  if (!s) return HSWEEP_ERR_OOM;
+  h->stw = s;
+  const Tree& t = h->tree;
+  s->P = std::min(kPMax, (h->strong_R + kOversample + 1) / 2 * 2);
+  std::vector<int> far, near, nrank;
+  strong_plan(t, h->strong_R, far, near, nrank);
+  for (int v = 2; v < h->nnodes; ++v)
+    if (nrank[v] > h->r_max) return HSWEEP_ERR_ARG;
+  std::vector<long long> soff;
+  long long so = 0;
+  for (size_t i = 0; i < far.size(); i += 8) {
+    soff.push_back(so);
+    so += (long long)(far[i + 4] + far[i + 5]) * s->P;
   }
   s->nfar = (int)soff.size();
   s->nnear = (int)(near.size() / 6);
@@ -461,6 +475,40 @@ int hsw_strong_project(hsweep_s* h, int m, const void* G_F, int* G_rank, void* G
   if (h->prec == HSWEEP_FP64)
     return project_impl<double>(h, m, (const c128*)G_F, G_rank, (c128*)G_F2, d_gfo, gf_entries);
   return project_impl<float>(h, m, (const c64*)G_F, G_rank, (c64*)G_F2, d_gfo, gf_entries);
+}
+
+extern "C" int hsweep_strong_plan(int n, int leaf, int R, int* nfar, int* nnear, int* far, int* near, int* ranks) {
+  if (n < 3 || n > 32767 || leaf < 2 || leaf > 8 || R < 1 || R > 8 || !nfar || !nnear) return HSWEEP_ERR_ARG;
+  Tree t;
+  t.build(n, leaf);
+  std::vector<int> fv, nv, rk;
+  strong_plan(t, R, fv, nv, rk);
+  *nfar = (int)(fv.size() / 8);
+  *nnear = (int)(nv.size() / 6);
+  if (far) std::copy(fv.begin(), fv.end(), far);
+  if (near) std::copy(nv.begin(), nv.end(), near);
+  if (ranks) std::copy(rk.begin(), rk.end(), ranks);
+  return HSWEEP_OK;
+}
+
+extern "C" int hsweep_rsvd_normals(uint32_t blk, uint32_t m, uint32_t seed, int rows, int P, double* out) {
+  if (rows < 0 || P < 2 || (P & 1) || (rows > 0 && !out)) return HSWEEP_ERR_ARG;
+  const double s = 2.3283064365386963e-10, two_pi = 6.283185307179586476925286766559;
+  for (int pr = 0; pr < P / 2; ++pr)
+    for (int row = 0; row < rows; ++row) {
+      const uint32_t ctr[4] = {(uint32_t)row, (uint32_t)pr, blk, m};
+      const uint32_t key[2] = {seed, 0x5EEDu};
+      uint32_t x[4];
+      hsw_philox4x32_10(ctr, key, x);
+      const double u0 = ((double)x[0] + 0.5) * s, u1 = (double)x[1] * s;
+      const double u2 = ((double)x[2] + 0.5) * s, u3 = (double)x[3] * s;
+      const double r0 = std::sqrt(-2.0 * std::log(u0)), r1 = std::sqrt(-2.0 * std::log(u2));
+      double* z0 = out + 2 * ((long long)(2 * pr) * rows + row);
+      double* z1 = out + 2 * ((long long)(2 * pr + 1) * rows + row);
+      z0[0] = r0 * std::cos(two_pi * u1); z0[1] = r0 * std::sin(two_pi * u1);
+      z1[0] = r1 * std::cos(two_pi * u3); z1[1] = r1 * std::sin(two_pi * u3);
+    }
+  return HSWEEP_OK;
 }
 
 extern "C" int hsweep_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
