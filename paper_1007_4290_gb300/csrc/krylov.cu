@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include "handle.h"
 
 namespace {
@@ -134,6 +135,11 @@ __global__ void scale_kernel(const c128* __restrict__ w, const double* __restric
     v[s * N + p] = cvt<double>(a * cvt<T>(w[s * N + p]));
 }
 
+// dst[i] = src[i] for n 8-byte words (the mailbox transfers below)
+__global__ void copy_words(const unsigned long long* __restrict__ src, unsigned long long* __restrict__ dst, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
 // r = f - y
 __global__ void sub_kernel(const c128* __restrict__ f, const c128* __restrict__ y, c128* __restrict__ r, long long n) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
@@ -153,7 +159,44 @@ struct KrylovWork {
   c128* coef = nullptr;        // [nrhs][vmax]
   double* nrm = nullptr;       // [nrhs]
   int vmax = 0;
+  // Mailbox for the solve's small host <-> device exchanges (Gram-Schmidt coefficients,
+  // norms, pointer tables, the status word): mapped pinned host memory moved by a copy
+  // kernel on the handle's stream instead of the copy engines, so that bulk transfers a
+  // caller runs beside the solve on another stream (the next batch's right-hand sides, the
+  // previous batch's solutions) never hold up its per-iteration exchanges.  Regions (bytes):
+  // coefficients up, norms up, one pointer up, the basis table up, results down.
+  unsigned char* mbox_h = nullptr;
+  unsigned char* mbox_d = nullptr;
+  size_t o_coef = 0, o_nrm = 0, o_tbl = 0, o_vtab = 0, o_down = 0, mbox_bytes = 0;
 };
+
+// bytes (a multiple of 8) from host src to device dst through the mailbox region `region`;
+// the region is rewritten only after a later stream synchronisation (the call sites below)
+static int mbox_up(hsweep_s* h, size_t region, const void* src, void* dst, size_t bytes) {
+  KrylovWork* k = h->kw;
+  if (bytes == 0) return HSWEEP_OK;
+  std::memcpy(k->mbox_h + region, src, bytes);
+  const int nw = (int)(bytes / 8);
+  copy_words<<<std::min(64, (nw + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<const unsigned long long*>(k->mbox_d + region), reinterpret_cast<unsigned long long*>(dst), nw);
+  h->nlaunch += 1;
+  HSW_CUDA(cudaGetLastError());
+  return HSWEEP_OK;
+}
+
+// bytes (a multiple of 8) from device src to host dst; synchronises the stream
+static int mbox_down(hsweep_s* h, const void* src, void* dst, size_t bytes) {
+  KrylovWork* k = h->kw;
+  if (bytes == 0) return HSWEEP_OK;
+  const int nw = (int)(bytes / 8);
+  copy_words<<<std::min(64, (nw + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<const unsigned long long*>(src), reinterpret_cast<unsigned long long*>(k->mbox_d + k->o_down), nw);
+  h->nlaunch += 1;
+  HSW_CUDA(cudaGetLastError());
+  HSW_CUDA(cudaStreamSynchronize(h->stream));
+  std::memcpy(dst, k->mbox_h + k->o_down, bytes);
+  return HSWEEP_OK;
+}
 
 void hsw_krylov_free(hsweep_s* h) {
   if (!h->kw) return;
@@ -161,6 +204,7 @@ void hsw_krylov_free(hsweep_s* h) {
   for (c128* p : k->V) hsw_release(h, p);
   void* ptrs[] = {k->d_V, k->r, k->z, k->w, k->t, k->d, k->partial, k->dots, k->coef, k->nrm};
   for (void* p : ptrs) hsw_release(h, p);
+  if (k->mbox_h) cudaFreeHost(k->mbox_h);
   delete k;
   h->kw = nullptr;
 }
@@ -184,6 +228,24 @@ static int krylov_reserve(hsweep_s* h, int nrhs) {
   A(k->coef, (size_t)nrhs * vmax * sizeof(c128));
   A(k->nrm, (size_t)nrhs * sizeof(double));
 #undef A
+  const size_t cb = ((size_t)nrhs * vmax * sizeof(c128) + 255) / 256 * 256;
+  const size_t nb = ((size_t)nrhs * sizeof(double) + 255) / 256 * 256;
+  const size_t vt = ((size_t)vmax * sizeof(c128*) + 255) / 256 * 256;
+  k->o_coef = 0;
+  k->o_nrm = cb;
+  k->o_tbl = cb + nb;
+  k->o_vtab = cb + nb + 256;
+  k->o_down = cb + nb + 256 + vt;
+  k->mbox_bytes = k->o_down + cb;
+  void* hp = nullptr;
+  if (cudaHostAlloc(&hp, k->mbox_bytes, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return HSWEEP_ERR_OOM;
+  }
+  k->mbox_h = static_cast<unsigned char*>(hp);
+  void* dp = nullptr;
+  HSW_CUDA(cudaHostGetDevicePointer(&dp, hp, 0));
+  k->mbox_d = static_cast<unsigned char*>(dp);
   return HSWEEP_OK;
 }
 
@@ -197,7 +259,8 @@ static int basis(hsweep_s* h, int i, c128** out) {
     k->V.push_back(p);
   }
   if (k->d_V_cap < (int)k->V.size()) {
-    HSW_CUDA(cudaMemcpyAsync(k->d_V, k->V.data(), k->V.size() * sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
+    int rc = mbox_up(h, k->o_vtab, k->V.data(), k->d_V, k->V.size() * sizeof(c128*));
+    if (rc) return rc;
     k->d_V_cap = (int)k->V.size();
   }
   *out = k->V[i];
@@ -215,9 +278,7 @@ static int batched_dots(hsweep_s* h, int first, int nv, const c128* w, int nrhs,
   h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   hd.resize((size_t)nrhs * nv);
-  HSW_CUDA(cudaMemcpyAsync(hd.data(), k->dots, (size_t)nrhs * nv * sizeof(c128), cudaMemcpyDeviceToHost, h->stream));
-  HSW_CUDA(cudaStreamSynchronize(h->stream));
-  return HSWEEP_OK;
+  return mbox_down(h, k->dots, hd.data(), (size_t)nrhs * nv * sizeof(c128));
 }
 
 // ||x[s]|| for every s, on the host
@@ -230,8 +291,8 @@ static int norms(hsweep_s* h, const c128* x, int nrhs, std::vector<double>& out,
   h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   std::vector<std::complex<double>> hd(nrhs);
-  HSW_CUDA(cudaMemcpyAsync(hd.data(), k->dots, nrhs * sizeof(c128), cudaMemcpyDeviceToHost, h->stream));
-  HSW_CUDA(cudaStreamSynchronize(h->stream));
+  int rc = mbox_down(h, k->dots, hd.data(), nrhs * sizeof(c128));
+  if (rc) return rc;
   out.resize(nrhs);
   for (int s = 0; s < nrhs; ++s) out[s] = std::sqrt(std::max(0.0, hd[s].real()));
   return HSWEEP_OK;
@@ -267,8 +328,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
   int rc = basis(h, 0, &v0);
   if (rc) return rc;
   {
-    std::vector<double> zn(znrm);
-    HSW_CUDA(cudaMemcpyAsync(k->nrm, zn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = mbox_up(h, k->o_nrm, znrm.data(), k->nrm, nrhs * sizeof(double)))) return rc;
     if (lowp) scale_kernel<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
     else scale_kernel<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(z, k->nrm, v0, N);
     h->nlaunch += 1;
@@ -290,14 +350,14 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     for (int pass = 0; pass < 2; ++pass) {
       if ((rc = batched_dots(h, 0, j + 1, k->w, nrhs, hd, lowp))) return rc;
       for (size_t e = 0; e < hd.size(); ++e) hcol[e] += hd[e];
-      HSW_CUDA(cudaMemcpyAsync(k->coef, hd.data(), hd.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
+      if ((rc = mbox_up(h, k->o_coef, hd.data(), k->coef, hd.size() * sizeof(c128)))) return rc;
       if (lowp) axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
       else axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
       h->nlaunch += 1;
     }
     std::vector<double> wn;
     if ((rc = norms(h, k->w, nrhs, wn, lowp))) return rc;
-    HSW_CUDA(cudaMemcpyAsync(k->nrm, wn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = mbox_up(h, k->o_nrm, wn.data(), k->nrm, nrhs * sizeof(double)))) return rc;
     if (lowp) scale_kernel<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
     else scale_kernel<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
     h->nlaunch += 1;
@@ -344,7 +404,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     std::vector<cd> Yc((size_t)nrhs * kmax, cd(0));
     for (int s = 0; s < nrhs; ++s)
       for (int i = 0; i < kmax; ++i) Yc[(size_t)s * kmax + i] = Y[(size_t)s * maxit + i];
-    HSW_CUDA(cudaMemcpyAsync(k->coef, Yc.data(), Yc.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = mbox_up(h, k->o_coef, Yc.data(), k->coef, Yc.size() * sizeof(c128)))) return rc;
     if (lowp) axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
     else axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
     h->nlaunch += 1;
@@ -403,8 +463,8 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       std::vector<std::complex<double>> one((size_t)nrhs, 0.0);
       for (int s = 0; s < nrhs; ++s) one[s] = active[s] ? 1.0 : 0.0;
       const c128* tbl[1] = {k->d};
-      HSW_CUDA(cudaMemcpyAsync(k->dots, tbl, sizeof(c128*), cudaMemcpyHostToDevice, h->stream));
-      HSW_CUDA(cudaMemcpyAsync(k->coef, one.data(), nrhs * sizeof(c128), cudaMemcpyHostToDevice, h->stream));
+      if ((rc = mbox_up(h, k->o_tbl, tbl, k->dots, sizeof(c128*)))) return rc;
+      if ((rc = mbox_up(h, k->o_coef, one.data(), k->coef, nrhs * sizeof(c128)))) return rc;
       axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->dots), 1,
                                                            k->coef, 1, 1.0, u, N);
       h->nlaunch += 1;
@@ -435,7 +495,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
     if (relres_out) relres_out[s] = fn[s] > 0 ? rn[s] / fn[s] : 0.0;
   }
   int st[2] = {0, -1};
-  HSW_CUDA(cudaMemcpy(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if ((rc = mbox_down(h, h->d_status, st, sizeof(st)))) return rc;
   if (st[0] != 0) return st[0];
   return all_done ? HSWEEP_OK : HSWEEP_ERR_NOT_CONVERGED;
 }
