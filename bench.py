@@ -248,7 +248,8 @@ def main():
                     help="comma-separated n: GMRES steps and times of the PML examples of Section 3.1 "
                          "(lens, waveguide, random medium; point source and wave packet), one JSON line")
     ap.add_argument("--strong-rank", type=int, default=0,
-                    help="with --direction-table / --boundary-table / --pml-table: strongly admissible H-matrices of "
+                    help="with --direction-table / --boundary-table / --pml-table / --apply-only / --setup-only: "
+                         "strongly admissible H-matrices of "
                          "rank R (Section 2.3; Section 3 uses R = 2) instead of weak ones of rank 2")
     args = ap.parse_args()
 
@@ -606,11 +607,12 @@ def run_parts(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = hs.hsweep_setup(c_d, w["omega"], w["pml"], w["eps_H"],
-                        hs.default_opts(precision=prec, team=args.team, groups=args.groups, sweep_tc=args.sweep_tc))
+                        hs.default_opts(precision=prec, team=args.team, groups=args.groups, sweep_tc=args.sweep_tc,
+                                        strong_rank=args.strong_rank))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     out = {"workload": args.workload, "n": n, "precision": "fp64" if args.fp64 else "mixed", "setup_s": setup_s,
-           "info": h.info()}
+           "strong_rank": args.strong_rank, "info": h.info()}
     if args.apply_only:
         nrhs = args.apply_only
         F = w["f"].reshape(w["f"].shape[0], -1)
