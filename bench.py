@@ -247,6 +247,11 @@ def main():
     ap.add_argument("--pml-table", default="",
                     help="comma-separated n: GMRES steps and times of the PML examples of Section 3.1 "
                          "(lens, waveguide, random medium; point source and wave packet), one JSON line")
+    ap.add_argument("--q-table", default="",
+                    help="comma-separated n (255,511,1023,2047 for q = 8..64): the PML examples at omega / 2 pi = 32 "
+                         "(Section 3.1, dependence on q), one JSON line")
+    ap.add_argument("--fields", default="1,2,3", help="with --pml-table / --q-table: velocity fields (1 lens, "
+                                                       "2 waveguide, 3 random medium)")
     ap.add_argument("--strong-rank", type=int, default=0,
                     help="with --direction-table / --boundary-table / --pml-table / --apply-only / --setup-only: "
                          "strongly admissible H-matrices of "
@@ -267,7 +272,7 @@ def main():
     if args.direction_table:
         run_direction_table(args)
         return
-    if args.pml_table:
+    if args.pml_table or args.q_table:
         run_pml_table(args)
         return
     if args.boundary_table:
@@ -571,8 +576,10 @@ def run_pml_table(args):
     import torch
     import paper_1007_4290_gb300 as hs
     rows = []
-    for n in [int(v) for v in args.pml_table.split(",")]:
-        for kind in ("pml1", "pml2", "pml3"):
+    sizes = args.pml_table or args.q_table
+    prefix = "pml" if args.pml_table else "qpml"
+    for n in [int(v) for v in sizes.split(",")]:
+        for kind in ["%s%s" % (prefix, k) for k in args.fields.split(",")]:
             w = synth.workload("%s_n%d" % (kind, n))
             kw, eps = _rank_opts(args, w)
             torch.cuda.synchronize()
@@ -592,8 +599,9 @@ def run_pml_table(args):
                 row[key] = {"iters": it[0], "solve_s": time.perf_counter() - t0, "relres": rr[0]}
             h.free()
             rows.append(row)
-    print(json.dumps({"metric": "GMRES steps, PML examples (Section 3.1, dependence on omega), %s, tol 1e-3"
-                                % _rank_label(args), "data": "synthetic", "rows": rows}))
+    what = "dependence on omega, q = 8" if args.pml_table else "dependence on q, omega / 2 pi = 32"
+    print(json.dumps({"metric": "GMRES steps, PML examples (Section 3.1, %s), %s, tol 1e-3"
+                                % (what, _rank_label(args)), "data": "synthetic", "rows": rows}))
 
 
 def run_parts(args):

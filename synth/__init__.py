@@ -198,6 +198,18 @@ def workload(name):
         f = np.stack([source_gaussian(n, (0.5, 0.125)),
                       source_wavepacket(n, (0.125, 0.125), (1.0, 1.0), omega, 1.0 / 16.0)])
         return dict(name=name, n=n, omega=omega, pml=8, eps_H=0.0, r_max=2, tol=1e-3, c=c, f=f)
+    if name.startswith(("qpml1_n", "qpml2_n", "qpml3_n")):
+        # Section 3.1, dependence on q: omega / 2 pi = 32 fixed, q = (n + 1) / 32 points per
+        # wavelength (n = 255, 511, 1023, 2047 for q = 8 .. 64), a PML of one wavelength
+        # (q cells), R = 2, tol 1e-3; the fields and forces of the pml workloads
+        kind, n = name.split("_n")
+        n = int(n)
+        w = workload("pml%s_n%d" % (kind[-1], n))
+        omega = two_pi * 32.0
+        q = (n + 1) // 32
+        f = np.stack([source_gaussian(n, (0.5, 0.125)),
+                      source_wavepacket(n, (0.125, 0.125), (1.0, 1.0), omega, 1.0 / 16.0)])
+        return dict(w, name=name, omega=omega, pml=max(2, q), f=f)
     if name.startswith(("depth1_n", "depth2_n", "mixed1_n", "mixed2_n")):
         # Section 3.2, other boundary conditions; q = 8, fixed rank R = 2, tol 1e-3, PML of
         # one wavelength (8 cells) on the sides in `pml_sides` (1: x1 = 0, 2: x1 = 1,
