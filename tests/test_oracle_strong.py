@@ -200,3 +200,29 @@ def test_strong_rank_two_preconditioner_converges_where_weak_rank_two_is_slower(
     u, _, _ = preconditioned_solve(A, S.apply, f, 1e-12, 100)
     u_ref = SparseLU(disc).solve(f)
     assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-9
+
+
+def _paper_steps():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_gmres_steps.txt")
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, om, q, n1, t1, t2 = line.split()
+            out[(key, int(n1), int(q))] = (int(t1), int(t2))
+    return out
+
+
+@pytest.mark.parametrize("field", [1, 2, 3])
+def test_strong_rank_two_sweep_takes_the_papers_steps_at_n_plus_1_128(field):
+    # the tables of Section 3.1 (dependence on omega) at omega / 2 pi = 16, q = 8: the
+    # oracle's strongly admissible H-sweep with R = 2 on the synthetic stand-ins for the
+    # pictured fields (synth.workload('pml{field}_n127')) takes the printed GMRES steps
+    # for both forces at tolerance 1e-3
+    want = _paper_steps()[("pml_field%d" % field, 128, 8)]
+    w = synth.workload("pml%d_n127" % field)
+    disc = Discretization(w["c"], w["omega"], w["pml"])
+    A = disc.matrix()
+    S = HSweep(disc, 0.0, leaf=8, rmax=2, admissibility="strong")
+    got = tuple(preconditioned_solve(A, S.apply, w["f"][s].ravel(), 1e-3, 50)[1] for s in range(2))
+    assert got == want, (got, want)
