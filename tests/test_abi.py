@@ -81,3 +81,12 @@ def test_strong_rank_argument_checks_without_gpu():
     o = hs.default_opts(strong_rank=3)
     rc = hs._lib.hsweep_setup(ctypes.c_void_p(16), 1.0, 2047, 16, 1e-6, ctypes.byref(o), None, ctypes.byref(raw))
     assert rc == hs.ERR_ARG and not raw.value
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # no CPU fallback: a missing libhsweep.so is an import-time error
+    _lib_path()
+    import pytest
+    import paper_1007_4290_gb300 as hs
+    with pytest.raises(ImportError):
+        hs.load_library(str(tmp_path / "libhsweep.so"))

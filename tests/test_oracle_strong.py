@@ -226,3 +226,26 @@ def test_strong_rank_two_sweep_takes_the_papers_steps_at_n_plus_1_128(field):
     S = HSweep(disc, 0.0, leaf=8, rmax=2, admissibility="strong")
     got = tuple(preconditioned_solve(A, S.apply, w["f"][s].ravel(), 1e-3, 50)[1] for s in range(2))
     assert got == want, (got, want)
+
+
+def test_rank_R_form_of_a_dense_matrix_is_the_blockwise_truncated_svd():
+    # from_dense with a rank cap R keeps, on every block of an interaction list, the best
+    # rank-R approximation (Eckart-Young: the error is the (R+1)-th singular value), and
+    # every dense block exactly
+    rng = np.random.default_rng(21)
+    n, R = 64, 2
+    ct = hs.Clusters(n, 4)
+    x = np.arange(n) / n
+    G = 1.0 / (1.0 + 40 * np.abs(x[:, None] - x[None, :])) + 0.01 * _rand(rng, n, n)
+    B = hs.from_dense(ct, G, Trunc(0.0, R))
+    for l, i, j, U, V in B.factor_blocks():
+        r0, r1 = ct.range(l, i)
+        c0, c1 = ct.range(l, j)
+        blk = G[r0:r1, c0:c1]
+        s = np.linalg.svd(blk, compute_uv=False)
+        assert U.shape[1] <= R
+        assert abs(np.linalg.norm(blk - U @ V.T, 2) - s[R]) <= 1e-10 * s[0]
+    for l, i, j, D in B.dense_blocks():
+        r0, r1 = ct.range(l, i)
+        c0, c1 = ct.range(l, j)
+        assert np.array_equal(D, G[r0:r1, c0:c1])
