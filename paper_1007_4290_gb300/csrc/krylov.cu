@@ -216,8 +216,7 @@ static int krylov_reserve(hsweep_s* h, int nrhs) {
   KrylovWork* k = new (std::nothrow) KrylovWork();
   if (!k) return HSWEEP_ERR_OOM;
   h->kw = k;
-  k->nrhs_cap = nrhs;
-  k->vmax = vmax;
+  k->vmax = vmax;   // nrhs_cap is set last: a failed reservation leaves a workspace of capacity 0
   const size_t vb = (size_t)nrhs * h->N * sizeof(c128);
   int rc;
 #define A(p, bytes) do { rc = hsw_alloc(h, (void**)&(p), (size_t)(bytes)); if (rc) return rc; } while (0)
@@ -246,6 +245,7 @@ static int krylov_reserve(hsweep_s* h, int nrhs) {
   void* dp = nullptr;
   HSW_CUDA(cudaHostGetDevicePointer(&dp, hp, 0));
   k->mbox_d = static_cast<unsigned char*>(dp);
+  k->nrhs_cap = nrhs;
   return HSWEEP_OK;
 }
 
