@@ -60,7 +60,8 @@ enum {
 enum {
   HSWEEP_FP64 = 0,  /* complex128 everywhere */
   HSWEEP_MIXED = 1  /* complex64 H-factors, setup products and sweeps; FP64 leaf
-                       inversions, GMRES (Arnoldi), residuals and iterative refinement */
+                       inversions, GMRES (Arnoldi orthogonalisation, A-products inside
+                       it), residuals and iterative refinement */
 };
 
 typedef struct {
@@ -74,11 +75,9 @@ typedef struct {
   int refine_max;    /* outer FP64 refinement steps in HSWEEP_MIXED (default 8) */
   int team;          /* CTAs per sweep team (power of two, 0 = automatic) */
   int groups;        /* right-hand sides per sweep team (1, 2, 4, 5 or 8; 0 = automatic) */
-  int sweep_kernel;  /* 0: automatic (default): the TMA-staged sweep on cooperative teams,
-                           else the TMA-staged sweep on clusters, else the basic sweep, the
-                           first whose shared-memory plan fits;
-                        1: the basic sweep that reads the factors from global memory;
-                        2: the TMA-staged sweep on thread-block clusters (else basic) */
+  int sweep_kernel;  /* 0: automatic (default): the bulk-copy-staged sweep on cooperative
+                           teams where its shared-memory plan fits, else the basic sweep;
+                        1: the basic sweep that reads the factors from global memory */
   int sweep_tc;      /* HSWEEP_MIXED team sweep, ancestor-level contractions: 0 on CUDA cores
                         (default, the faster on GB300); 1 the reductions, 2 the reductions
                         and the expansion, with mma.sync tensor-core instructions (TF32
@@ -95,11 +94,7 @@ typedef struct {
   int pml_sides;     /* bit mask of the sides with a PML: 1 x1 = 0, 2 x1 = 1, 4 x2 = 0, 8 x2 = 1
                         (default 15, all four); a side without one is a Dirichlet boundary
                         (Section 2.5), zero unless data is moved in by hsweep_boundary_rhs.
-                        hsweep_setup requires a PML on the side where the sweep starts
-                        (x2 = 0 upward, x2 = 1 downward) and returns HSWEEP_ERR_ARG otherwise:
-                        next to a Dirichlet side the first Schur complements have no
-                        absorption (a downward sweep of the depth-extrapolation problem met
-                        the GMRES test with a wrong solution in testing) */
+                        The sweep may start at either kind of side. */
   int strong_rank;   /* 0 (default): weakly admissible H-matrices (siblings are each other's
                         interaction list; Section 2.3).  R = 1..8: the strongly admissible
                         case (Section 2.3; the configuration of the experiments of Section 3,
@@ -112,6 +107,15 @@ typedef struct {
                         layout with rank 3 R (L - depth) + leaf at each depth, and r_max is
                         raised to 3 R (L - 1) + leaf when smaller (HSWEEP_ERR_ARG above 56) */
   unsigned rsvd_seed; /* key of the Philox4x32-10 generator of those test vectors (default 0) */
+  int krylov_lowp;   /* HSWEEP_MIXED only.  0 (default): every operation of the inner GMRES
+                        (Gram-Schmidt dots and updates, norms, scalings, the product with A)
+                        computes in FP64.  1: those operations compute in FP32 on the
+                        FP64-stored vectors (products and per-thread partial sums in FP32,
+                        block and global sums in FP64); the outer residual f - A u, the
+                        update u += d and the reported residuals stay FP64.  Faster on GPUs
+                        whose FP64 units are slow.  In either arithmetic the inner solve of
+                        HSWEEP_MIXED targets at most a relative 4e-6 (the refinement reaches
+                        the tolerance). */
 } hsweep_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -192,8 +196,9 @@ HSWEEP_API int hsweep_matvec(hsweep_t h, const hsw_c128* x, hsw_c128* y, int nrh
  * Solve A u = f for nrhs right-hand sides by GMRES on M A u = M f (Section 2.4),
  * unrestarted, x0 = u on entry (pass zeros for the default start).  Each RHS stops
  * when ||M (f - A u)|| <= tol ||M f||.  In HSWEEP_MIXED the preconditioned solve is
- * wrapped in FP64 iterative refinement on the true residual f - A u until
- * ||f - A u|| <= tol_true ||f|| with tol_true = tol (at most refine_max steps).
+ * wrapped in FP64 iterative refinement: every outer step recomputes r = f - A u in FP64
+ * and z = M r, stops the RHS when ||z|| <= tol ||M f||, and otherwise runs GMRES on
+ * M A d = z and sets u += d (at most refine_max outer steps).
  *   f, u        device [nrhs][N]
  *   iters_out   host int[nrhs] or NULL: Arnoldi steps taken (summed over refinement)
  *   relres_out  host double[nrhs] or NULL: final ||f - A u|| / ||f|| (FP64)
@@ -281,8 +286,8 @@ HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
 
 /*
  * The launch plan the apply would use for nrhs right-hand sides (diagnostics):
- * out[0] the sweep kernel (0: basic, 1: TMA-staged on thread-block clusters, 2: TMA-staged
- * on cooperative teams exchanging tagged partial sums), out[1] CTAs per team, out[2] right-hand sides per team,
+ * out[0] the sweep kernel (0: basic, 2: bulk-copy-staged on cooperative teams exchanging
+ * tagged partial sums; 1 is not used), out[1] CTAs per team, out[2] right-hand sides per team,
  * out[3] teams, out[4] 1 for a whole-grid team with a grid barrier, out[5] dynamic shared
  * memory per CTA in bytes, out[6] largest per-step factor record of one CTA in bytes,
  * out[7] column slices per row in the expansion (0 for the basic kernel).
@@ -301,9 +306,11 @@ HSWEEP_API int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8);
  *     library reserves until the process exits.  A call whose scratch need
  *     (about nrhs * n*n * 8 bytes in HSWEEP_MIXED, * 16 in HSWEEP_FP64, plus a few MiB)
  *     exceeds it returns HSWEEP_ERR_ARG and does nothing.
- *   - The first call on a device looks up the array's device address (once per
- *     device, with the handle's device current); make that first call before any
- *     stream capture.  The current device must be the handle's device.
+ *   - The array's device address is looked up when the handle is created
+ *     (hsweep_setup / hsweep_create, on the handle's device) and kept in the handle;
+ *     this call makes no lookup.  The current device must be the handle's device.
+ *   - Downward handles (sweep_dir = -1) are refused with HSWEEP_ERR_ARG (their apply
+ *     needs reflected copies of r and z).
  *   - Every call shares the one array and it keeps the last call's contents; calls
  *     whose GPU work overlaps (other streams, other handles, other threads) race on it.
  *   - r and z are as in hsweep_apply.  No cudaMalloc, cudaFree or allocating library

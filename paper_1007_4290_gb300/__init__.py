@@ -37,7 +37,8 @@ class hsweep_opts(ctypes.Structure):
                 ("refine_max", ctypes.c_int), ("team", ctypes.c_int), ("groups", ctypes.c_int),
                 ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int),
                 ("sweep_dir", ctypes.c_int), ("pml_sides", ctypes.c_int),
-                ("strong_rank", ctypes.c_int), ("rsvd_seed", ctypes.c_uint)]
+                ("strong_rank", ctypes.c_int), ("rsvd_seed", ctypes.c_uint),
+                ("krylov_lowp", ctypes.c_int)]
 
 
 class HSweepError(RuntimeError):

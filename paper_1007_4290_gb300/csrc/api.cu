@@ -3,21 +3,35 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
 #include "handle.h"
+
+// Test hook: HSWEEP_FAIL_ALLOC_AT=k (or "k:label") makes the k-th device allocation
+// counted from the moment the variable took its current value fail with HSWEEP_ERR_OOM;
+// a new value (another k or label) restarts the count, so one process can fail every
+// allocation of a sequence in turn.
+static bool alloc_hook_fires() {
+  static std::mutex mu;
+  static std::string last;
+  static long long counter = 0, fail_at = -1;
+  std::lock_guard<std::mutex> lock(mu);
+  const char* e = getenv("HSWEEP_FAIL_ALLOC_AT");
+  const std::string cur = e ? e : "";
+  if (cur != last) {
+    last = cur;
+    counter = 0;
+    fail_at = cur.empty() ? -1 : atoll(cur.c_str());
+  }
+  ++counter;
+  return fail_at > 0 && counter == fail_at;
+}
 
 int hsw_alloc(hsweep_s* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  // test hook: HSWEEP_FAIL_ALLOC_AT=k makes the k-th allocation of a process fail
-  static long long counter = 0;
-  static long long fail_at = -2;
-  if (fail_at == -2) {
-    const char* e = getenv("HSWEEP_FAIL_ALLOC_AT");
-    fail_at = e ? atoll(e) : -1;
-  }
-  ++counter;
-  if (fail_at > 0 && counter == fail_at) return HSWEEP_ERR_OOM;
+  if (alloc_hook_fires()) return HSWEEP_ERR_OOM;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -56,6 +70,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->pml_sides = 15;
   o->strong_rank = 0;
   o->rsvd_seed = 0;
+  o->krylov_lowp = 0;
   return HSWEEP_OK;
 }
 
@@ -90,10 +105,10 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       !(eps_H >= 0) || opt.leaf < 2 || opt.leaf > 8 || opt.r_max < 1 || opt.r_max > 56 ||
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
-      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
+      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 1 ||
       opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
       (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15 ||
-      opt.strong_rank < 0 || opt.strong_rank > 8)
+      opt.strong_rank < 0 || opt.strong_rank > 8 || opt.krylov_lowp < 0 || opt.krylov_lowp > 1)
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -125,6 +140,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
 #define TRYC(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); destroy(h); return HSWEEP_ERR_CUDA; } } while (0)
   TRYC(cudaGetDevice(&h->device));
   TRYC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  hsw_noalloc_bind(h);
 
   // factor-store layout (identical for every layer)
   h->off.assign(h->nnodes, 0);
@@ -197,15 +213,6 @@ extern "C" int hsweep_create(const double* c_dev, double omega, int n, int pml_w
 extern "C" int hsweep_setup(const double* c_dev, double omega, int n, int pml_width, double eps_H,
                             const hsweep_opts* opt, void* stream, hsweep_t* out) {
   if (!out) return HSWEEP_ERR_ARG;
-  {
-    // the sweep must start at a side with a PML: next to a Dirichlet side the first
-    // Schur complements have no absorption and the factorisation is not reliable
-    hsweep_opts o;
-    hsweep_default_opts(&o);
-    if (opt) o = *opt;
-    const int start_bit = o.sweep_dir < 0 ? 8 : 4;
-    if (pml_width > 0 && (o.pml_sides & start_bit) == 0) return HSWEEP_ERR_ARG;
-  }
   hsweep_t h = nullptr;
   int rc = create_impl(c_dev, omega, n, pml_width, eps_H, opt, stream, &h);
   if (rc != HSWEEP_OK) return rc;
@@ -427,7 +434,6 @@ extern "C" int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
 extern "C" int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8) {
   if (!h || !out8 || nrhs < 1) return HSWEEP_ERR_ARG;
   if (h->opt.sweep_kernel == 0 && hsw_team_plan(h, nrhs, out8)) return HSWEEP_OK;
-  if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) return hsw_tma_plan(h, nrhs, out8);
   for (int i = 0; i < 8; ++i) out8[i] = 0;
   return HSWEEP_OK;
 }

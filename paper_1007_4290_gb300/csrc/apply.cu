@@ -447,11 +447,6 @@ int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs) {
     int rc = hsw_apply_team(h, r, z, nrhs, &used);
     if (rc != HSWEEP_OK || used) return rc;
   }
-  if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) {
-    bool used = false;
-    int rc = hsw_apply_tma(h, r, z, nrhs, &used);
-    if (rc != HSWEEP_OK || used) return rc;
-  }
   SweepConfig cfg = choose_config(h, nrhs);
   if (h->prec == HSWEEP_FP64) return apply_impl<double>(h, r, z, nrhs, cfg);
   return apply_impl<float>(h, r, z, nrhs, cfg);
@@ -468,10 +463,6 @@ size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs) {
   if (h->opt.sweep_kernel == 0) {
     const size_t fl = hsw_apply_team_scratch_bytes(h, nrhs);
     if (fl > 0) return fl;
-  }
-  if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) {
-    const size_t tma = hsw_apply_tma_scratch_bytes(h, nrhs);
-    if (tma > 0) return tma;
   }
   SweepConfig cfg = choose_config(h, nrhs);
   const long long es = h->prec == HSWEEP_FP64 ? (long long)sizeof(c128) : (long long)sizeof(c64);
@@ -525,11 +516,6 @@ int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scrat
   if (h->opt.sweep_kernel == 0) {      // the same kernel hsw_apply would use
     bool used = false;
     int rc = hsw_apply_team(h, r, z, nrhs, &used, scratch, bytes);
-    if (rc != HSWEEP_OK || used) return rc;
-  }
-  if (h->opt.sweep_kernel == 0 || h->opt.sweep_kernel == 2) {
-    bool used = false;
-    int rc = hsw_apply_tma(h, r, z, nrhs, &used, scratch, bytes);
     if (rc != HSWEEP_OK || used) return rc;
   }
   SweepConfig cfg = choose_config(h, nrhs);

@@ -87,14 +87,17 @@ int hsw_grad(hsweep_s* h, const c128* f, int nsrc, const int* rec, int nrec, con
   if (rc != HSWEEP_OK) { cleanup(); return rc; }
   receiver_residual<<<nsrc, 256, 0, h->stream>>>(U, N, rec, nrec, d, res, jpart);
   h->nlaunch += 1;
-  cudaMemsetAsync(B, 0, (size_t)nsrc * N * sizeof(c128), h->stream);
+  if (cudaGetLastError() != cudaSuccess) { cleanup(); return HSWEEP_ERR_CUDA; }
+  if (cudaMemsetAsync(B, 0, (size_t)nsrc * N * sizeof(c128), h->stream) != cudaSuccess) { cleanup(); return HSWEEP_ERR_CUDA; }
   adjoint_rhs<<<dim3((nrec + 255) / 256, nsrc), 256, 0, h->stream>>>(res, rec, nrec, N, B);
   h->nlaunch += 1;
+  if (cudaGetLastError() != cudaSuccess) { cleanup(); return HSWEEP_ERR_CUDA; }
   if (cudaMemsetAsync(V, 0, (size_t)nsrc * N * sizeof(c128), h->stream) != cudaSuccess) { cleanup(); return HSWEEP_ERR_CUDA; }
   rc = hsw_solve(h, B, V, nsrc, tol, it.data(), rr.data());
   if (rc != HSWEEP_OK) { cleanup(); return rc; }
   gradient_kernel<<<1216, 256, 0, h->stream>>>(U, V, nsrc, N, h->d_c, h->d_s1s2, h->omega, grad);
   h->nlaunch += 1;
+  if (cudaGetLastError() != cudaSuccess) { cleanup(); return HSWEEP_ERR_CUDA; }
   std::vector<double> hj(nsrc);
   if (cudaMemcpyAsync(hj.data(), jpart, nsrc * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {

@@ -94,6 +94,10 @@ struct hsweep_s {
 
   std::vector<void*> allocs;   // every device allocation owned by the handle
 
+  // device address of the library's fixed scratch array for hsweep_apply_noalloc, looked
+  // up on the handle's device when the handle is created (noalloc.cu); null if that failed
+  void* noalloc_scratch = nullptr;
+
   // instrumentation: kernel launches made by this handle, and (when prof is set) a
   // pair of CUDA events around every sweep-kernel launch on the handle's stream
   long long nlaunch = 0;
@@ -115,17 +119,14 @@ int hsw_boundary_rhs(hsweep_s* h, int side, const c128* b, c128* f, int nrhs);
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
 // the same product with FP32 arithmetic (lowp) on the FP64 vectors
 int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp);
+// noalloc.cu: look up the fixed scratch array on the current (the handle's) device
+void hsw_noalloc_bind(hsweep_s* h);
 // apply.cu
 int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs);
 size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs);
 int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scratch, size_t bytes);
 // pack.cu
 int hsw_pack(hsweep_s* h, int m0, int m1);
-// sweep_tma.cu
-int hsw_apply_tma(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch = nullptr,
-                  size_t scratch_bytes = 0);
-size_t hsw_apply_tma_scratch_bytes(hsweep_s* h, int nrhs);
-int hsw_tma_plan(hsweep_s* h, int nrhs, long long* out8);
 // sweep_team.cu
 int hsw_apply_team(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch = nullptr,
                    size_t scratch_bytes = 0);

@@ -5,11 +5,14 @@
 //     otherwise GMRES on M A d = z (x0 = 0) and u += d.
 // In HSWEEP_FP64 a converged inner solve ends the loop (its residual estimate is the
 // FP64 one); in HSWEEP_MIXED, where M runs in complex64, every outer step re-checks
-// the FP64 residual (iterative refinement), and the inner GMRES computes in FP32 on
-// FP64-stored vectors (its target is a relative 4e-6 at most; the FP64 arithmetic units
-// of this GPU run at about 1/60 of the FP32 rate): per-thread products and partial sums
-// in FP32, block and global sums in FP64.  The residual f - A u, the update u += d and
-// the reported residuals stay FP64.
+// the FP64 residual (iterative refinement).  The inner GMRES (Arnoldi by Gram-Schmidt,
+// norms, scalings, the product with A) computes in FP64 in both modes.  The option
+// krylov_lowp moves it to FP32 arithmetic on the FP64-stored vectors in HSWEEP_MIXED
+// (the FP64 units of this GPU run at about 1/60 of the FP32 rate): per-thread products
+// and partial sums in FP32, block and global sums in FP64.  In HSWEEP_MIXED the inner
+// target is a relative 4e-6 at most in either arithmetic (the complex64 sweeps make M A
+// accurate to a few 1e-7 only); the outer refinement reaches the tolerance.  The residual f - A u, the update u += d and the reported
+// residuals stay FP64 in every case.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -312,7 +315,8 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
   KrylovWork* k = h->kw;
   const int maxit = h->opt.gmres_max_it;
   const long long N = h->N;
-  const bool lowp = h->prec == HSWEEP_MIXED;   // FP32 arithmetic on FP64-stored vectors
+  // FP32 arithmetic on the FP64-stored vectors only when asked for (HSWEEP_MIXED)
+  const bool lowp = h->prec == HSWEEP_MIXED && h->opt.krylov_lowp != 0;
   typedef std::complex<double> cd;
   std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(maxit + 1) * maxit, cd(0)));
   std::vector<std::vector<cd>> cs(nrhs, std::vector<cd>(maxit)), sn(nrhs, std::vector<cd>(maxit));
@@ -420,11 +424,12 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
   KrylovWork* k = h->kw;
   const long long N = h->N;
   const bool mixed = h->prec == HSWEEP_MIXED;
+  const bool lowp = mixed && h->opt.krylov_lowp != 0;
   std::vector<int> iters(nrhs, 0);
   std::vector<double> Mfn, fn, zn, est(nrhs, 1.0);
   // ||M f|| (the reference of the stopping test) and ||f||
   if ((rc = hsw_apply(h, f, k->z, nrhs))) return rc;
-  if ((rc = norms(h, k->z, nrhs, Mfn, mixed))) return rc;
+  if ((rc = norms(h, k->z, nrhs, Mfn, lowp))) return rc;
   if ((rc = norms(h, f, nrhs, fn))) return rc;
   // with a zero initial guess the first residual is f itself and M r = M f is at hand
   std::vector<double> un;
@@ -443,7 +448,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
       h->nlaunch += 1;
       if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
-      if ((rc = norms(h, k->z, nrhs, zn, mixed))) return rc;
+      if ((rc = norms(h, k->z, nrhs, zn, lowp))) return rc;
     }
     std::vector<char> active(nrhs, 0);
     std::vector<double> eta(nrhs, 0.0);
@@ -454,6 +459,8 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       active[s] = 1;
       all_done = false;
       const double need = tol * Mfn[s] / zn[s];
+      // in HSWEEP_MIXED the complex64 sweeps leave M A accurate to a few 1e-7, so the inner
+      // solve is asked for no more than a relative 4e-6 and the refinement does the rest
       eta[s] = mixed ? std::max(0.5 * need, 4e-6) : 0.9 * need;
     }
     if (all_done) break;
@@ -486,7 +493,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
   if ((rc = norms(h, k->r, nrhs, rn))) return rc;
   if (!all_done && mixed) {
     if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
-    if ((rc = norms(h, k->z, nrhs, zn, mixed))) return rc;
+    if ((rc = norms(h, k->z, nrhs, zn, lowp))) return rc;
     all_done = true;
     for (int s = 0; s < nrhs; ++s) if (!(zn[s] <= tol * Mfn[s])) all_done = false;
   }

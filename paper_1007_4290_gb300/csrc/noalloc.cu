@@ -3,8 +3,10 @@
 // Its scratch (the cache of T~_m u_m between the two sweeps and the exchange slots of
 // the sweep teams) lives in the fixed device array below instead of buffers allocated
 // on demand.  The array is defined at file scope, so every GPU that loads this library
-// reserves it until the process exits.
-#include <mutex>
+// reserves it until the process exits.  In host code the array's name is only a
+// host-side stand-in: its device address is looked up with cudaGetSymbolAddress when a
+// handle is created (on the handle's device, which is current then) and kept in the
+// handle, whose lifetime cannot exceed the context the address belongs to.
 #include "handle.h"
 
 namespace {
@@ -13,29 +15,16 @@ constexpr size_t kNoAllocScratchBytes = HSWEEP_NOALLOC_SCRATCH_BYTES;   // 32 Mi
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once per
-// device (in host code the array's name is only a host-side stand-in).
-int scratch_address(int dev, void** out) {
-  if (dev < 0 || dev >= kMaxDevices) return HSWEEP_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return HSWEEP_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
-  return HSWEEP_OK;
-}
-
 }  // namespace
+
+void hsw_noalloc_bind(hsweep_s* h) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  h->noalloc_scratch = p;
+}
 
 extern "C" int hsweep_apply_noalloc(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!r || !z))) return HSWEEP_ERR_ARG;
@@ -49,9 +38,7 @@ extern "C" int hsweep_apply_noalloc(hsweep_t h, const hsw_c128* r, hsw_c128* z, 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return HSWEEP_ERR_CUDA; }
   if (dev != h->device) return HSWEEP_ERR_ARG;
-  void* scratch = nullptr;
-  int rc = scratch_address(dev, &scratch);
-  if (rc != HSWEEP_OK) return rc;
-  return hsw_apply_scratch(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs, scratch,
-                           kNoAllocScratchBytes);
+  if (!h->noalloc_scratch) return HSWEEP_ERR_CUDA;
+  return hsw_apply_scratch(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs,
+                           h->noalloc_scratch, kNoAllocScratchBytes);
 }

@@ -31,6 +31,7 @@
 // a padded stride, read as 16-byte pairs where G is even.  In complex64 the
 // multiply-adds use the paired FP32 instruction fma.rn.f32x2: with a = sum (Re f) x and
 // b = sum (Im f) x, f x = (Re a - Im b, Im a + Re b).
+#include <cstdlib>
 #include <type_traits>
 #include "handle.h"
 #include "tma.cuh"
@@ -210,6 +211,10 @@ struct TeamArgs {
   Cx<R>* w;
   typename Tagged<R>::W* xch;   // ancestors' tagged partial sums: [2][nteams][C][dC][rcap][G]
   int* status;
+  long long wait_limit;         // iterations of the waits for other CTAs' partial sums
+                                // (kWaitLimit unless a test shortens it; the waits for this
+                                // CTA's own bulk copies always allow kWaitLimit)
+  int withhold;                 // test only: this CTA never publishes its partial sums (-1: none)
   // shared-memory plan (byte offsets)
   unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_etab[2], o_x[2],
       o_qanc, o_qloc, o_mbar, o_flags;
@@ -512,8 +517,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
         if (rl == 0 && k < qcap && (k < r || d <= dC)) {
           if (d <= dC) {
             typename T::W* dst = xpart + ((long long)c * dC + (d - 1)) * a.rcap * G + k * G;
+            if ((int)blockIdx.x != a.withhold)
 #pragma unroll
-            for (int g = 0; g < G; ++g) T::store(dst + g, T::pack(k < r ? out[g] : Cx<R>(0, 0), tag));
+              for (int g = 0; g < G; ++g) T::store(dst + g, T::pack(k < r ? out[g] : Cx<R>(0, 0), tag));
           } else {
             Cx<R>* dst = qloc + dt[DT_QBASE + d] + (jn * qcap + k) * GS;
 #pragma unroll
@@ -627,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
                   pending = true;
                 }
             if (!pending) break;
-            if (++spins > kWaitLimit || *(volatile int*)a.status != 0) {
+            if (++spins > a.wait_limit || *(volatile int*)a.status != 0) {
               report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
               *s_fail = 1;
               break;
@@ -647,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
               typename T::W v = T::load(src[j] + u * cstride);
               long long spins = 0;
               while (!T::ok(v, tag)) {
-                if (++spins > kWaitLimit || *(volatile int*)a.status != 0) {
+                if (++spins > a.wait_limit || *(volatile int*)a.status != 0) {
                   report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
                   *s_fail = 1;
                   break;
@@ -1066,6 +1072,16 @@ static int apply_team_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
   a.w = reinterpret_cast<Cx<R>*>(wptr);
   a.xch = reinterpret_cast<typename Tagged<R>::W*>(xptr);
   a.status = h->d_status;
+  // test hooks (environment): HSWEEP_TEST_WAIT_LIMIT shortens the waits for other CTAs,
+  // HSWEEP_TEST_WITHHOLD=c makes CTA c of the grid never publish its partial sums, so
+  // that the CTAs reading them run out of their waits and report HSWEEP_ERR_TIMEOUT
+  a.wait_limit = kWaitLimit;
+  a.withhold = -1;
+  if (const char* e = getenv("HSWEEP_TEST_WAIT_LIMIT")) {
+    const long long v = atoll(e);
+    if (v > 0 && v < kWaitLimit) a.wait_limit = v;
+  }
+  if (const char* e = getenv("HSWEEP_TEST_WITHHOLD")) a.withhold = atoi(e);
   const bool prof = h->prof;
   if (scratch) h->prof = false;   // the no-allocation path creates no events
   int rc = HSWEEP_OK;

@@ -17,6 +17,14 @@ def shard(count, world, rank):
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def _reduce_device(group=None):
+    """The device of the all-reduce buffer, the same on every rank whatever its shard:
+    this process's current CUDA device under NCCL, the host otherwise."""
+    if dist.is_initialized() and dist.get_backend(group) == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
 def sharded_misfit_gradient(grad_fn, F, d, group=None):
     """Misfit and gradient summed over all sources when each rank owns a slice of them.
 
@@ -34,8 +42,7 @@ def sharded_misfit_gradient(grad_fn, F, d, group=None):
     else:
         J, g = 0.0, None
     n_grad = int(F[0].numel()) if torch.is_tensor(F) else int(F[0].size)
-    dev = g.device if g is not None else (F.device if torch.is_tensor(F) else torch.device("cpu"))
-    buf = torch.zeros(n_grad + 1, dtype=torch.float64, device=dev)
+    buf = torch.zeros(n_grad + 1, dtype=torch.float64, device=_reduce_device(group))
     if g is not None:
         buf[:n_grad] = g
     buf[n_grad] = float(J)

@@ -104,19 +104,17 @@ def test_apply_full_rank_blocks_and_repeat_calls_agree(hs):
     h.free()
 
 
-@pytest.mark.parametrize("kernel", [0, 2])
 @pytest.mark.parametrize("n,prec,nrhs,team", [(127, 0, 1, 0), (127, 1, 9, 0), (255, 0, 2, 32), (255, 1, 64, 0),
                                               (64, 1, 3, 4), (37, 0, 2, 0), (255, 1, 17, 0), (255, 0, 5, 0)])
-def test_tma_sweeps_match_basic_sweep_and_exact(hs, n, prec, nrhs, team, kernel):
-    # kernel 0: the automatic choice (the cooperative-team kernel where it fits);
-    # kernel 2: the thread-block-cluster kernel
+def test_team_sweep_matches_basic_sweep_and_exact(hs, n, prec, nrhs, team):
+    # the automatic choice (the cooperative-team kernel) against the basic kernel on the
+    # same factors, and against the exact sweep of the exported layers
     c, omega, pml = _problem(n, 4)
     disc = Discretization(c, omega, pml)
     h1 = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6,
-                         hs.default_opts(precision=prec, team=team, sweep_kernel=kernel))
+                         hs.default_opts(precision=prec, team=team))
     plan = h1.sweep_plan(nrhs)
-    if kernel == 0:
-        assert plan["tma"] == 2, plan
+    assert plan["tma"] == 2, plan
     R = torch.randn(nrhs, n * n, dtype=torch.complex128, device="cuda")
     Z1 = h1.apply(R)
     # the same factors through the basic kernel: rebuild a handle with identical setup

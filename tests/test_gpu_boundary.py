@@ -58,9 +58,11 @@ def test_boundary_data_forcing_term_matches_oracle(hs, side, direction):
     assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("name,direction", [("depth1_n127", 1), ("depth2_n127", 1), ("mixed1_n127", 1),
-                                            ("mixed2_n127", 1), ("mixed1_n127", -1)])
+@pytest.mark.parametrize("name", ["depth1_n127", "depth2_n127", "mixed1_n127", "mixed2_n127"])
+@pytest.mark.parametrize("direction", [1, -1])
 def test_boundary_problems_solve_to_the_direct_solution(hs, name, direction):
+    # both sweep directions; the downward sweeps of depth1, depth2 and mixed2 start at a
+    # Dirichlet side (no absorption in the first Schur complements)
     w = synth.workload(name)
     n = w["n"]
     disc = Discretization(w["c"], w["omega"], w["pml"], pml_sides=w["pml_sides"])
@@ -76,10 +78,3 @@ def test_boundary_problems_solve_to_the_direct_solution(hs, name, direction):
     h.free()
     u = u.cpu().numpy()[0]
     assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-7, it
-
-
-@pytest.mark.parametrize("name,direction", [("depth1_n127", -1), ("mixed2_n127", -1)])
-def test_setup_refuses_a_sweep_that_starts_at_a_dirichlet_side(hs, name, direction):
-    w = synth.workload(name)
-    with pytest.raises(hs.HSweepError):
-        _handle(hs, w, direction)

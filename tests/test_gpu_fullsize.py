@@ -33,6 +33,9 @@ def _true_relres(disc, U, F):
 
 
 def test_n1023_random_batched_mixed(hs):
+    # eight of the workload's 64 point sources in one batched mixed-precision solve, every
+    # one against the direct solve of A u = f (one sparse LU of A) at the metric's relative
+    # error 1e-6, and through the FP64 true residual
     w = synth.workload("n1023_random")
     n, omega, pml = w["n"], w["omega"], w["pml"]
     F = w["f"][:8].reshape(8, n * n)
@@ -44,10 +47,12 @@ def test_n1023_random_batched_mixed(hs):
     rel = _true_relres(disc, U, F)
     assert np.all(rel < 1e-6), (rel, it)
     assert max(it) <= 12
-    # one source against the direct solve of A u = f
-    u_ref = spla.splu(disc.matrix().tocsc()).solve(F[0])
-    err = np.linalg.norm(U[0] - u_ref) / np.linalg.norm(u_ref)
-    assert err < 1e-5, err
+    lu = spla.splu(disc.matrix().tocsc())
+    errs = []
+    for s in range(8):
+        u_ref = lu.solve(F[s])
+        errs.append(np.linalg.norm(U[s] - u_ref) / np.linalg.norm(u_ref))
+    assert max(errs) < 1e-6, errs
 
 
 @pytest.fixture(scope="module")

@@ -108,9 +108,8 @@ def test_rank_two_strong_solve_reaches_the_direct_solution(hs):
 
 @pytest.mark.parametrize("name", ["mixed1_n63", "depth1_n63", "dir_n63"])
 def test_rank_two_iteration_counts_track_the_oracle_strong_sweep(hs, name):
-    # Section 3 protocol: R = 2, GMRES tolerance 1e-3.  The GPU projects an accurate weak
-    # inverse instead of truncating inside every H-operation, so it may converge faster;
-    # it must not be more than two steps slower than the oracle's strong H-sweep.
+    # Section 3 protocol: R = 2, GMRES tolerance 1e-3: the GPU's steps within two of the
+    # oracle's strong H-sweep
     w = synth.workload(name)
     n = w["n"]
     sides = w.get("pml_sides", 15)
@@ -125,7 +124,7 @@ def test_rank_two_iteration_counts_track_the_oracle_strong_sweep(hs, name):
     fg = torch.tensor(f.reshape(1, n * n), device="cuda")
     _, it, rr = h.solve(fg, 1e-3)
     h.free()
-    assert it[0] <= it_oracle + 2, (it, it_oracle)
+    assert abs(it[0] - it_oracle) <= 2, (it, it_oracle)
 
 
 @pytest.mark.parametrize("name", ["pml1_n127", "pml2_n127", "pml3_n127"])

@@ -75,6 +75,41 @@ def test_sharded_gradient_and_bench_rank_logic():
     assert not np.array_equal(out[0][3], out[1][3])
 
 
+def _worker_more_ranks_than_sources(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1007_4290_gb300.distributed import sharded_misfit_gradient
+        c, omega, pml, F, rec, d = _problem()
+        F, d = F[:2], d[:2]
+
+        def grad_fn(Fl, dl):
+            J, g, _ = adjoint.misfit_and_gradient(c, omega, pml, np.asarray(Fl), rec, np.asarray(dl))
+            return J, torch.tensor(g.ravel())
+
+        J, g = sharded_misfit_gradient(grad_fn, F, d)
+        out[rank] = (J, g.numpy(), str(g.device))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_gradient_with_more_ranks_than_sources():
+    # world size 3, two sources: one rank owns nothing and still joins the one all-reduce
+    # with a buffer on the same device type as the others
+    world, port = 3, _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker_more_ranks_than_sources, args=(world, port, out), nprocs=world, join=True)
+    c, omega, pml, F, rec, d = _problem()
+    J_ref, g_ref, _ = adjoint.misfit_and_gradient(c, omega, pml, F[:2], rec, d[:2])
+    for r in range(world):
+        J, g, dev = out[r]
+        assert dev == "cpu"
+        assert abs(J - J_ref) <= 1e-12 * J_ref
+        np.testing.assert_allclose(g, g_ref.ravel(), rtol=0, atol=1e-12 * np.max(np.abs(g_ref)))
+
+
 def test_shard_covers_everything_once():
     from paper_1007_4290_gb300.distributed import shard
     for count in (0, 1, 5, 64):

@@ -3,9 +3,11 @@
 synchronisation is not allowed, an exhausted memory budget).  Its scratch is a fixed
 32 MiB device array inside the library instead of on-demand buffers.
 
-It must give the same result as hsweep_apply, on two calls in a row (the array keeps
-the previous call's contents), and refuse requests larger than the array.  This file
-is collected last so that a stop at the first failure has already run every other test.
+It runs the same deterministic kernel as hsweep_apply, so its result must be identical,
+on two calls in a row (the array keeps the previous call's contents); the device's free
+memory must not change across the call; requests larger than the array are refused.
+This file is collected last so that a stop at the first failure has already run every
+other test.
 """
 import numpy as np
 import pytest
@@ -16,21 +18,29 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,prec,nrhs", [(64, 0, 1), (127, 1, 3), (127, 0, 2)])
-def test_noalloc_apply_matches_apply_twice(n, prec, nrhs):
+# sweep_kernel 0: the cooperative-team kernel (the automatic choice at these sizes);
+# sweep_kernel 1: the basic kernel
+@pytest.mark.parametrize("n,prec,nrhs,kernel", [(64, 0, 1, 0), (127, 1, 3, 0), (127, 0, 2, 0), (127, 1, 2, 1),
+                                                (64, 0, 3, 1)])
+def test_noalloc_apply_matches_apply_twice(n, prec, nrhs, kernel):
     import paper_1007_4290_gb300 as hs
     c = synth.velocity_random(n, 1 / 8, 1)
     omega, pml = 2 * np.pi * (n + 1) / 12, max(2, (n + 1) // 8)
-    h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6, hs.default_opts(precision=prec))
-    tol = 1e-12 if prec == hs.FP64 else 2e-5
+    h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6,
+                        hs.default_opts(precision=prec, sweep_kernel=kernel))
+    assert (h.sweep_plan(nrhs)["tma"] == 2) == (kernel == 0)
     for call in range(2):
         r = torch.randn(nrhs, n * n, dtype=torch.complex128, device="cuda")
         ref = h.apply(r)
         z = torch.empty_like(r)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
         hs.hsweep_apply_noalloc(h, r, z)
         torch.cuda.synchronize()
-        err = (torch.linalg.norm(z - ref) / torch.linalg.norm(ref)).item()
-        assert err < tol, (call, err)
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (call, free0, free1)
+        assert torch.equal(z, ref), call
+    assert h.status()[0] == 0
     h.free()
 
 
