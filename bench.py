@@ -357,6 +357,8 @@ def main():
     ap.add_argument("--setup-only", action="store_true", help="time only the setup sweep (Algorithm 2.5)")
     ap.add_argument("--team", type=int, default=0, help="with --apply-only: CTAs per sweep team (0 = automatic)")
     ap.add_argument("--groups", type=int, default=0, help="with --apply-only: right-hand sides per team (0 = automatic)")
+    ap.add_argument("--team-threads", type=int, default=0,
+                    help="with --apply-only: threads per CTA of the team sweep (512, 256; 0 = automatic)")
     ap.add_argument("--sweep-tc", type=int, default=0, help="with --apply-only: ancestor contractions on tensor cores")
     ap.add_argument("--boundary-table", default="",
                     help="comma-separated n: GMRES steps and times of the boundary-condition examples of "
@@ -547,6 +549,28 @@ def main():
     roof["algorithmic_flops_per_launch"] = flops
     roof["algorithmic_bytes_per_launch"] = bytes_
 
+    # the apply alone at 1 and 16 right-hand sides (the HBM-bound end of the sweep): CUDA
+    # events around each launch, achieved bandwidth of the algorithmic bytes
+    apply_hbm = {}
+    for nr in (1, 16):
+        Rn = f_d[:nr].clone()
+        Zn = torch.empty_like(Rn)
+        for _ in range(3):
+            h.apply(Rn, Zn)
+        h.stats(reset=True)
+        h.profile(True)
+        for _ in range(10):
+            h.apply(Rn, Zn)
+        h.profile(False)
+        _, sw_n, swms_n = h.stats(reset=True)
+        fl_n, by_n, _ = sweep_work(h, n, nr, info["bytes_per_entry"])
+        t_n = swms_n / max(1, sw_n) / 1e3
+        pk, _ = _peaks()
+        apply_hbm[str(nr)] = {"launch_ms": t_n * 1e3, "algorithmic_bytes": by_n, "gbs": by_n / t_n / 1e9,
+                              "hbm_frac": by_n / t_n / 1e9 / pk["hbm_gbs"], "tflops": fl_n / t_n / 1e12,
+                              "us_per_layer_step": t_n * 1e6 / (2 * n - 1)}
+        del Rn, Zn
+
     # the mixed solution of source 0 (the last timed step's), for its error against the
     # direct solve of the CPU leg
     u_mixed0 = u_d[0].cpu().numpy() if rank == 0 else None
@@ -631,6 +655,7 @@ def main():
             "gpu_launches": launches,
             "sweep_launches_per_step": sweeps / args.steps,
             "roofline": roof,
+            "apply_only": apply_hbm,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -779,7 +804,7 @@ def run_parts(args):
     t0 = time.perf_counter()
     h = hs.hsweep_setup(c_d, w["omega"], w["pml"], w["eps_H"],
                         hs.default_opts(precision=prec, team=args.team, groups=args.groups, sweep_tc=args.sweep_tc,
-                                        strong_rank=args.strong_rank))
+                                        strong_rank=args.strong_rank, team_threads=args.team_threads))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     out = {"workload": args.workload, "n": n, "precision": "fp64" if args.fp64 else "mixed", "setup_s": setup_s,

@@ -94,7 +94,12 @@ typedef struct {
   int pml_sides;     /* bit mask of the sides with a PML: 1 x1 = 0, 2 x1 = 1, 4 x2 = 0, 8 x2 = 1
                         (default 15, all four); a side without one is a Dirichlet boundary
                         (Section 2.5), zero unless data is moved in by hsweep_boundary_rhs.
-                        The sweep may start at either kind of side. */
+                        The sweep may start at either kind of side.  When it starts at a side
+                        without a PML, the factorisation is built for the operator with a PML
+                        of the same width and profile on that side (without absorption the
+                        Schur-complement recursion amplifies truncation and rounding errors
+                        from layer to layer); hsweep_matvec and the GMRES of hsweep_solve use
+                        the true operator, so the solution is that of the stated problem. */
   int strong_rank;   /* 0 (default): weakly admissible H-matrices (siblings are each other's
                         interaction list; Section 2.3).  R = 1..8: the strongly admissible
                         case (Section 2.3; the configuration of the experiments of Section 3,
@@ -107,6 +112,8 @@ typedef struct {
                         layout with rank 3 R (L - depth) + leaf at each depth, and r_max is
                         raised to 3 R (L - 1) + leaf when smaller (HSWEEP_ERR_ARG above 56) */
   unsigned rsvd_seed; /* key of the Philox4x32-10 generator of those test vectors (default 0) */
+  int team_threads;  /* threads per CTA of the team sweep: 512 (one CTA per SM), 256 (two CTAs
+                        per SM, half the rows per CTA) or 0 (default: the launch plan chooses) */
   int krylov_lowp;   /* HSWEEP_MIXED only.  0 (default): every operation of the inner GMRES
                         (Gram-Schmidt dots and updates, norms, scalings, the product with A)
                         computes in FP64.  1: those operations compute in FP32 on the
@@ -198,7 +205,10 @@ HSWEEP_API int hsweep_matvec(hsweep_t h, const hsw_c128* x, hsw_c128* y, int nrh
  * when ||M (f - A u)|| <= tol ||M f||.  In HSWEEP_MIXED the preconditioned solve is
  * wrapped in FP64 iterative refinement: every outer step recomputes r = f - A u in FP64
  * and z = M r, stops the RHS when ||z|| <= tol ||M f||, and otherwise runs GMRES on
- * M A d = z and sets u += d (at most refine_max outer steps).
+ * M A d = z and sets u += d (at most refine_max outer steps).  An outer step whose ||z||
+ * is at most 5e4 tol ||M f|| and whose inner GMRES reached 0.5 tol ||M f|| ends the loop
+ * without another apply: the complex64 sweep departs from a linear map by less than 1e-5
+ * relative, so the remaining ||M (f - A u)|| stays below tol ||M f||.
  *   f, u        device [nrhs][N]
  *   iters_out   host int[nrhs] or NULL: Arnoldi steps taken (summed over refinement)
  *   relres_out  host double[nrhs] or NULL: final ||f - A u|| / ||f|| (FP64)
@@ -288,7 +298,8 @@ HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
  * The launch plan the apply would use for nrhs right-hand sides (diagnostics):
  * out[0] the sweep kernel (0: basic, 2: bulk-copy-staged on cooperative teams exchanging
  * tagged partial sums; 1 is not used), out[1] CTAs per team, out[2] right-hand sides per team,
- * out[3] teams, out[4] 1 for a whole-grid team with a grid barrier, out[5] dynamic shared
+ * out[3] teams, out[4] for the basic kernel 1 when its team is the whole grid (a grid barrier),
+ * for the team kernel the threads per CTA (512: one CTA per SM, 256: two), out[5] dynamic shared
  * memory per CTA in bytes, out[6] largest per-step factor record of one CTA in bytes,
  * out[7] column slices per row in the expansion (0 for the basic kernel).
  */

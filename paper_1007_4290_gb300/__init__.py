@@ -38,7 +38,7 @@ class hsweep_opts(ctypes.Structure):
                 ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int),
                 ("sweep_dir", ctypes.c_int), ("pml_sides", ctypes.c_int),
                 ("strong_rank", ctypes.c_int), ("rsvd_seed", ctypes.c_uint),
-                ("krylov_lowp", ctypes.c_int)]
+                ("team_threads", ctypes.c_int), ("krylov_lowp", ctypes.c_int)]
 
 
 class HSweepError(RuntimeError):
@@ -200,7 +200,8 @@ class Handle:
     def sweep_plan(self, nrhs):
         out = (ctypes.c_longlong * 8)()
         _check(_lib.hsweep_sweep_plan(self.raw, nrhs, out), "hsweep_sweep_plan")
-        keys = ["tma", "team_ctas", "rhs_per_team", "teams", "grid", "smem", "record_bytes_max", "leaves_per_chunk"]
+        keys = ["tma", "team_ctas", "rhs_per_team", "teams", "grid_or_threads", "smem", "record_bytes_max",
+                "leaves_per_chunk"]
         return dict(zip(keys, list(out)))
 
     def layer_ranks(self, m):

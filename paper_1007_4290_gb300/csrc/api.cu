@@ -70,6 +70,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->pml_sides = 15;
   o->strong_rank = 0;
   o->rsvd_seed = 0;
+  o->team_threads = 0;
   o->krylov_lowp = 0;
   return HSWEEP_OK;
 }
@@ -108,7 +109,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 1 ||
       opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
       (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15 ||
-      opt.strong_rank < 0 || opt.strong_rank > 8 || opt.krylov_lowp < 0 || opt.krylov_lowp > 1)
+      opt.strong_rank < 0 || opt.strong_rank > 8 || opt.krylov_lowp < 0 || opt.krylov_lowp > 1 ||
+      (opt.team_threads != 0 && opt.team_threads != 256 && opt.team_threads != 512))
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -196,7 +198,24 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
     // the reflected problem of a downward sweep swaps the layers at x2 = 0 and x2 = 1
     int sides = opt.pml_sides;
     if (h->dir < 0) sides = (sides & 3) | ((sides & 4) << 1) | ((sides & 8) >> 1);
-    TRY(hsw_assemble(h, opt.pml_C, opt.pml_form, sides));
+    TRY(hsw_assemble(h, opt.pml_C, opt.pml_form, sides, h->d_diag, h->d_east, h->d_north, h->d_s1s2));
+    h->d_diag_m = h->d_diag;
+    h->d_east_m = h->d_east;
+    h->d_north_m = h->d_north;
+    if (pml_width > 0 && (sides & 4) == 0) {
+      // The sweep starts at a Dirichlet side (x2 = 0 of the stored problem).  Without
+      // absorption there, the Schur-complement recursion S_m = A_mm - A T_{m-1} A amplifies
+      // truncation and rounding errors from layer to layer (the perturbation of T_m is
+      // about a^2 T_m dT_{m-1} T_m, with a^2 ~ 1/h^4 and |T_m| no longer small), and the
+      // factorised T~_m drift from the exact ones within a few wavelengths.  The
+      // factorisation is therefore built for the operator with an absorbing layer of the
+      // same width and profile on that side; GMRES still solves the true A u = f.
+      TRY(hsw_alloc(h, (void**)&h->d_diag_m, N * sizeof(c128)));
+      TRY(hsw_alloc(h, (void**)&h->d_east_m, (size_t)n * (n + 1) * sizeof(c128)));
+      TRY(hsw_alloc(h, (void**)&h->d_north_m, (size_t)(n + 1) * n * sizeof(c128)));
+      TRY(hsw_assemble(h, opt.pml_C, opt.pml_form, sides | 4, h->d_diag_m, h->d_east_m, h->d_north_m, nullptr));
+      h->start_absorber = true;
+    }
   }
   TRYC(cudaStreamSynchronize(h->stream));
 #undef TRY

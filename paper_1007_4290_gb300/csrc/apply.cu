@@ -418,7 +418,7 @@ static int apply_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, const Sweep
   a.N = h->N; a.layer_stride = h->layer_stride;
   a.lo = h->d_lo; a.sz = h->d_sz; a.off = h->d_off;
   a.fac = reinterpret_cast<const Cx<R>*>(h->d_fac);
-  a.rank = h->d_rank; a.north = h->d_north;
+  a.rank = h->d_rank; a.north = h->d_north_m;
   a.r = r; a.z = z;
   a.w = reinterpret_cast<Cx<R>*>(h->d_wcache);
   a.xch = reinterpret_cast<Cx<R>*>(h->d_xch);
@@ -483,7 +483,7 @@ static int apply_scratch_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, con
   a.N = h->N; a.layer_stride = h->layer_stride;
   a.lo = h->d_lo; a.sz = h->d_sz; a.off = h->d_off;
   a.fac = reinterpret_cast<const Cx<R>*>(h->d_fac);
-  a.rank = h->d_rank; a.north = h->d_north;
+  a.rank = h->d_rank; a.north = h->d_north_m;
   a.r = r; a.z = z;
   a.w = reinterpret_cast<Cx<R>*>(scratch);
   a.xch = reinterpret_cast<Cx<R>*>(scratch + align_up((long long)nrhs * h->N * (long long)es, 256));

@@ -41,7 +41,7 @@ __global__ void assemble_kernel(int n, double h, double eta, double pref, double
   north[(long long)j * n + i] = n_l;
   if (j == n - 1) north[(long long)n * n + i] = n_r;
   c128 ss = si * sj;
-  s1s2[p] = ss;
+  if (s1s2) s1s2[p] = ss;
   double cc = c[p];
   c128 k2 = (omega * omega / (cc * cc)) * cinv(ss);
   diag[p] = k2 - (((e_l + e_r) + n_l) + n_r);
@@ -111,12 +111,13 @@ __global__ void matvec_kernel(int n, long long N, int nrhs, const c128* __restri
 
 }  // namespace
 
-int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides) {
+int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides, c128* diag, c128* east, c128* north,
+                 c128* s1s2) {
   double eta = h->pml_width * h->h;
   double pref = (pml_form == 0 && eta > 0) ? pml_C / eta : pml_C;
   dim3 grid(div_up(h->n, 128), h->n);
-  assemble_kernel<<<grid, 128, 0, h->stream>>>(h->n, h->h, eta, pref, h->omega, pml_sides, h->d_c,
-                                                h->d_diag, h->d_east, h->d_north, h->d_s1s2);
+  assemble_kernel<<<grid, 128, 0, h->stream>>>(h->n, h->h, eta, pref, h->omega, pml_sides, h->d_c, diag, east, north,
+                                                s1s2);
   h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   return HSWEEP_OK;

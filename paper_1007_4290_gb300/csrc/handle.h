@@ -58,6 +58,13 @@ struct hsweep_s {
   c128* d_east = nullptr;
   c128* d_north = nullptr;
   c128* d_s1s2 = nullptr;
+  // the operator the sweeping factorisation is built for (setup and the apply's layer
+  // couplings): the arrays above, except when the sweep starts at a side without a PML;
+  // then its own arrays, assembled with an absorbing layer on that side (api.cu)
+  c128* d_diag_m = nullptr;
+  c128* d_east_m = nullptr;
+  c128* d_north_m = nullptr;
+  bool start_absorber = false;
 
   // Leaf-major packed copy of the factors, read by the sweep: for every layer and leaf
   // one contiguous record [leaf block | rows of the leaf in F_v for depths 1..L], so the
@@ -66,9 +73,9 @@ struct hsweep_s {
   long long pack_stride = 0;             // entries per layer (worst-case capacity)
   long long* d_recoff = nullptr;         // [n][nleaves + 1] record offsets within a layer
   std::vector<long long> slab_bytes_max; // per slab depth dC: largest slab record in bytes
-  // team-sweep launch plans already chosen: {nrhs, ok, dC, C, G, teams, smem}; cleared
-  // whenever the packed factors change
-  std::vector<std::array<long long, 7>> team_plans;
+  // team-sweep launch plans already chosen: {nrhs, ok, dC, C, G, teams, smem, threads per
+  // CTA}; cleared whenever the packed factors change
+  std::vector<std::array<long long, 8>> team_plans;
   int rank_max = 0;
   bool pack_valid = false;
 
@@ -112,8 +119,10 @@ struct hsweep_s {
 int hsw_alloc(hsweep_s* h, void** p, size_t bytes);
 void hsw_release(hsweep_s* h, void* p);
 
-// assemble.cu
-int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides);
+// assemble.cu: the operator with PMLs on the sides in pml_sides into diag/east/north
+// (and s1s2 unless null)
+int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides, c128* diag, c128* east, c128* north,
+                 c128* s1s2);
 // Dirichlet data b on one side as a forcing term on the adjacent layer (Section 2.5)
 int hsw_boundary_rhs(hsweep_s* h, int side, const c128* b, c128* f, int nrhs);
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);

@@ -13,13 +13,20 @@
 //     S_t^{-1} = diag(G_a, G_b) - Y M Y^t.
 // The new off-diagonal block is -Y_a M12 Y_b^t; the diagonal corrections -Y_a M11 Y_a^t
 // and -Y_b M22 Y_b^t are rank-k updates of every block below a and b ("hadd" with a
-// factorised term).  All nodes of one depth are processed by the same launches, and
-// every block that received columns is recompressed once per depth ("Matrix
-// addition": QR of both factors, SVD of the small core, truncation at eps_H relative to
-// the block's largest singular value, at most r_max terms).  QR is classical
+// factorised term).  All nodes of one depth are processed by the same launches.
+// Recompression ("Matrix addition": QR of both factors, SVD of the small core,
+// truncation at eps_H relative to the block's largest singular value, at most r_max
+// terms) runs once per layer, after the last depth, on every block whose final core fits
+// the SVD's shared memory: appended columns accumulate (up to depth x (r_max + 1) of
+// them), the untruncated factors feed the products of the higher depths, and each block
+// is truncated once, in its final form.  Blocks whose core would not fit (large blocks
+// in complex128) are recompressed after every depth that changed them.  A small block whose factors have at least as
+// many columns as rows takes the dense path: its core is the block itself, C = F_a F_b^t,
+// and its new factors come straight from the SVD of C (no QR).  QR is classical
 // Gram-Schmidt with re-orthogonalisation; the SVD is one-sided (Hestenes) Jacobi.
 // The leaf inverses are computed in FP64 with partial pivoting in both precisions.
 #include <algorithm>
+#include <cmath>
 #include <utility>
 #include "handle.h"
 
@@ -61,12 +68,16 @@ template <typename R> __device__ R block_sum(R v, R* red) {
 }
 
 struct Geo {          // tree and buffer geometry passed by value to every kernel
-  int n, L, leaf, nnodes, r_max, KCAP, WCAP;
+  int n, L, leaf, nnodes, r_max, KCAP, WCAP, QCAP;
   const int* lo;
   const int* sz;
   const int* rowleaf;      // [n] leaf node of each row
   const long long* sfo;    // S factor offsets (capacity KCAP per node)
-  const long long* gfo;    // G factor offsets (capacity WCAP per node)
+  const long long* gfo;    // G factor offsets (capacity cap[v] columns per node)
+  const int* cap;          // column capacity of every node's G factor
+  const long long* qro;    // offsets of the reductions Qr (cap[v] x KCAP per node)
+  const long long* rbo;    // offsets of the R factors (min(sz, cap) x cap, row-major, ld cap)
+  const int* list;         // recompression kernels: the nodes (or left siblings) to process
 };
 
 __device__ __forceinline__ int depth_of(int v) { return 31 - __clz(v); }
@@ -144,10 +155,16 @@ __global__ void leaf_inverse(Geo g, int m, const Cx<R>* __restrict__ S_leaf, Cx<
     int a = e / (2 * lf), b = e % (2 * lf);
     A[a][b] = b < lf ? cvt<double>(src[b * lf + a]) : c128(a == b - lf ? 1.0 : 0.0, 0.0);
   }
+  __shared__ double s_red[4];
   __syncthreads();
-  double scale = 0;
-  for (int a = 0; a < lf; ++a)
-    for (int b = 0; b < lf; ++b) scale = fmax(scale, sqrt(abs2(A[a][b])));
+  // the largest squared modulus of the leaf's entries (one entry per thread, then warps)
+  double scale2 = 0;
+  for (int e = threadIdx.x; e < lf * lf; e += blockDim.x) scale2 = fmax(scale2, abs2(A[e / lf][e % lf]));
+  for (int o = 16; o > 0; o >>= 1) scale2 = fmax(scale2, __shfl_xor_sync(0xffffffffu, scale2, o));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = scale2;
+  __syncthreads();
+  scale2 = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) scale2 = fmax(scale2, s_red[i]);
   bool bad = false;
   for (int k = 0; k < lf; ++k) {
     if (threadIdx.x == 0) {
@@ -164,7 +181,7 @@ __global__ void leaf_inverse(Geo g, int m, const Cx<R>* __restrict__ S_leaf, Cx<
     }
     __syncthreads();
     const c128 pv = A[k][k];
-    if (!(sqrt(abs2(pv)) > 1e-14 * scale)) { bad = true; break; }
+    if (!(abs2(pv) > 1e-28 * scale2)) { bad = true; break; }   // |pivot| <= 1e-14 max |entry|
     const c128 ip = cinv(pv);
     __syncthreads();
     if (threadIdx.x < 2 * lf) A[k][threadIdx.x] = A[k][threadIdx.x] * ip;
@@ -201,7 +218,7 @@ __global__ void tsmm_reduce(Geo g, int d, const Cx<R>* __restrict__ G_F, const i
   const int s = g.sz[u], ld_x = g.sz[nu], xo = g.lo[u] - g.lo[nu];
   const Cx<R>* F = G_F + g.gfo[u];
   const Cx<R>* X = S_F + g.sfo[nu];
-  Cx<R>* out = Qr + (long long)u * g.r_max * g.KCAP;
+  Cx<R>* out = Qr + g.qro[u];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int kr = warp; kr < ru; kr += nw) {
     for (int c0 = 0; c0 < k; c0 += 8) {
@@ -246,7 +263,7 @@ __global__ void tsmm_expand(Geo g, int d, const Cx<R>* __restrict__ G_leaf, cons
     const int u = lam >> (g.L - du);
     const int ru = G_rank[u];
     const Cx<R>* F = G_F + g.gfo[u] + (row - g.lo[u]);
-    const Cx<R>* q = Qr + (long long)(u ^ 1) * g.r_max * g.KCAP + col;
+    const Cx<R>* q = Qr + g.qro[u ^ 1] + col;
     const int s = g.sz[u];
     for (int kr = 0; kr < ru; ++kr) cfma(y, F[(long long)kr * s], q[kr * g.KCAP]);
   }
@@ -441,22 +458,34 @@ __global__ void woodbury_append(Geo g, int d, const int* __restrict__ S_rank, co
 }
 
 // ---------------------------------------------------------------------------------
-// Recompression, step 1: Gram-Schmidt QR (twice-orthogonalised) of F_u in place; the
-// Q columns are compacted to the independent ones and R (qc x w) written out.
+// Recompression, step 1, for the nodes u = list[blockIdx.x]: with w = rank(u) columns,
+// a factor with at least as many columns as rows (w >= sz(u)) takes the dense path,
+// Q = I and R = F_u (qcols = sz(u), qmode = 1); otherwise Gram-Schmidt QR (twice
+// orthogonalised) of F_u in place, the Q columns compacted to the independent ones and
+// R (qc x w) written out (qmode = 0).  R is row-major with leading dimension cap(u).
 template <typename R>
-__global__ void qr_cgs2(Geo g, int d, Cx<R>* __restrict__ G_F, const int* __restrict__ G_rank,
-                        Cx<R>* __restrict__ Rb, int* __restrict__ qcols) {
+__global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ G_rank, Cx<R>* __restrict__ Rb,
+                        int* __restrict__ qcols, int* __restrict__ qmode) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int u = (1 << (d + 1)) + blockIdx.x;
-  const int s = g.sz[u], w = G_rank[u];
+  const int u = g.list[blockIdx.x];
+  const int s = g.sz[u], w = G_rank[u], ld = g.cap[u];
   Cx<R>* F = G_F + g.gfo[u];
-  Cx<R>* Rm = Rb + (long long)u * g.WCAP * g.WCAP;      // row-major qc x w, ld WCAP
+  Cx<R>* Rm = Rb + g.rbo[u];                               // row-major qc x w, ld cap(u)
+  if (w >= s && s <= g.QCAP) {
+    for (int e = threadIdx.x; e < s * w; e += blockDim.x) {
+      const int i = e % s, l = e / s;
+      Rm[(long long)i * ld + l] = F[e];
+    }
+    if (threadIdx.x == 0) { qcols[u] = s; qmode[u] = 1; }
+    return;
+  }
   Cx<R>* v = reinterpret_cast<Cx<R>*>(sm);                // [s]
-  Cx<R>* c = v + s;                                        // [WCAP]
-  R* red = reinterpret_cast<R*>(c + g.WCAP);               // [32]
+  Cx<R>* c = v + s;                                        // [QCAP]
+  R* red = reinterpret_cast<R*>(c + g.QCAP);               // [32]
   __shared__ int s_qc;
   if (threadIdx.x == 0) s_qc = 0;
-  for (int e = threadIdx.x; e < g.WCAP * w; e += blockDim.x) Rm[(e / w) * g.WCAP + e % w] = Cx<R>(0, 0);
+  const int rows = min(s, ld);
+  for (int e = threadIdx.x; e < rows * w; e += blockDim.x) Rm[(long long)(e / w) * ld + e % w] = Cx<R>(0, 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = 0; j < w; ++j) {
@@ -475,7 +504,7 @@ __global__ void qr_cgs2(Geo g, int d, Cx<R>* __restrict__ G_F, const int* __rest
         acc = warp_sum(acc);
         if (lane == 0) {
           c[l] = acc;
-          Rm[l * g.WCAP + j] += acc;
+          Rm[(long long)l * ld + j] += acc;
         }
       }
       __syncthreads();
@@ -493,7 +522,7 @@ __global__ void qr_cgs2(Geo g, int d, Cx<R>* __restrict__ G_F, const int* __rest
       const R sn = sqrt(nr), is = R(1) / sn;
       for (int i = threadIdx.x; i < s; i += blockDim.x) F[(long long)qc * s + i] = is * v[i];
       if (threadIdx.x == 0) {
-        Rm[qc * g.WCAP + j] = Cx<R>(sn, 0);
+        Rm[(long long)qc * ld + j] = Cx<R>(sn, 0);
         s_qc = qc + 1;
       }
     } else if (threadIdx.x == 0) {
@@ -501,28 +530,44 @@ __global__ void qr_cgs2(Geo g, int d, Cx<R>* __restrict__ G_F, const int* __rest
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) qcols[u] = s_qc;
+  if (threadIdx.x == 0) { qcols[u] = s_qc; qmode[u] = 0; }
 }
 
-// Recompression, step 2: for every sibling pair (a, b), C = R_a R_b^t (qa x qb), one-sided
-// Jacobi C W = P Sigma, truncation, and the small transforms
+// Recompression, step 2: for every sibling pair (a, b) with a = list[blockIdx.x],
+// C = R_a R_b^t (qa x qb), one-sided Jacobi C W = P Sigma, truncation, and the small
+// transforms
 //   T_a = (P Sigma)[:, kept] (qa x k'),  T_b = conj(W)[:, kept] (qb x k').
+// qa, qb <= QCAP, the largest core of the plan (setup_alloc).
+// Shuffle-sum within aligned groups of GW lanes (GW = 16 or 32).
+template <typename R> __device__ __forceinline__ R group_sum_r(R v, int GW) {
+  for (int o = GW >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename R> __device__ __forceinline__ Cx<R> group_sum(Cx<R> v, int GW) {
+  for (int o = GW >> 1; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
+
 template <typename R>
-__global__ void svd_jacobi(Geo g, int d, double eps, const Cx<R>* __restrict__ Rb, const int* __restrict__ qcols,
+__global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Rb, const int* __restrict__ qcols,
                            const int* __restrict__ G_rank, Cx<R>* __restrict__ Wb, Cx<R>* __restrict__ Tx,
-                           int* __restrict__ newrank) {
+                           int* __restrict__ newrank, int smem_entries) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int t = (1 << d) + blockIdx.x;
-  const int a = 2 * t, b = 2 * t + 1;
+  const int a = g.list[blockIdx.x], b = a + 1, t = a >> 1;
   const int qa = qcols[a], qb = qcols[b], w = G_rank[a];
-  Cx<R>* C = reinterpret_cast<Cx<R>*>(sm);          // column-major qa x qb (ld qa)
-  R* sig = reinterpret_cast<R*>(C + (size_t)qa * qb);   // [qb]
-  int* order = reinterpret_cast<int*>(sig + qb + 1);    // [qb]
+  // C (column-major qa x qb, ld qa) and, when both fit in the shared-memory plan, the
+  // accumulated rotations W (column-major qb x qb, ld qb); otherwise W stays in Wb
+  const bool w_shared = (long long)qa * qb + (long long)qb * qb <= smem_entries;
+  Cx<R>* C = reinterpret_cast<Cx<R>*>(sm);
+  Cx<R>* Wm = w_shared ? C + (size_t)qa * qb : Wb + (long long)t * g.QCAP * g.QCAP;
+  const int ldw = w_shared ? qb : g.QCAP;
+  R* sig = reinterpret_cast<R*>(reinterpret_cast<Cx<R>*>(sm) + smem_entries);   // [QCAP + 1]
+  int* order = reinterpret_cast<int*>(sig + g.QCAP + 1);                          // [QCAP]
   __shared__ int s_rot, s_keep;
   __shared__ R s_scale;
-  Cx<R>* Wm = Wb + (long long)t * g.WCAP * g.WCAP;   // column-major qb x qb (ld WCAP)
-  const Cx<R>* Ra = Rb + (long long)a * g.WCAP * g.WCAP;
-  const Cx<R>* Rbm = Rb + (long long)b * g.WCAP * g.WCAP;
+  const Cx<R>* Ra = Rb + g.rbo[a];
+  const Cx<R>* Rbm = Rb + g.rbo[b];
+  const int lda = g.cap[a], ldb = g.cap[b];
   if (qa == 0 || qb == 0) {
     if (threadIdx.x == 0) { newrank[a] = 0; newrank[b] = 0; }
     return;
@@ -530,12 +575,12 @@ __global__ void svd_jacobi(Geo g, int d, double eps, const Cx<R>* __restrict__ R
   for (int e = threadIdx.x; e < qa * qb; e += blockDim.x) {
     const int i = e % qa, j = e / qa;
     Cx<R> acc(0, 0);
-    for (int l = 0; l < w; ++l) cfma(acc, Ra[i * g.WCAP + l], Rbm[j * g.WCAP + l]);
+    for (int l = 0; l < w; ++l) cfma(acc, Ra[(long long)i * lda + l], Rbm[(long long)j * ldb + l]);
     C[e] = acc;
   }
   for (int e = threadIdx.x; e < qb * qb; e += blockDim.x) {
     const int i = e % qb, j = e / qb;
-    Wm[(long long)j * g.WCAP + i] = Cx<R>(i == j ? 1 : 0, 0);
+    Wm[(long long)j * ldw + i] = Cx<R>(i == j ? 1 : 0, 0);
   }
   __syncthreads();
   // normalise by the largest column norm
@@ -562,43 +607,52 @@ __global__ void svd_jacobi(Geo g, int d, double eps, const Cx<R>* __restrict__ R
   for (int e = threadIdx.x; e < qa * qb; e += blockDim.x) C[e] = iscale * C[e];
   __syncthreads();
   const int me = qb + (qb & 1);               // even number of positions (one dummy if odd)
+  // one group of GW lanes per column pair: whole warps while there are at most as many
+  // pairs as warps, half warps beyond (every pair of a round in one pass)
+  const int GW = (me / 2 <= nw) ? 32 : 16;
+  const int gpw = 32 / GW;                    // groups per warp
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < me - 1; ++round) {
-      for (int pr = warp; pr < me / 2; pr += nw) {
+      // the loop bound is uniform over the warp, so every lane reaches every shuffle
+      for (int pb = warp * gpw; pb < me / 2; pb += nw * gpw) {
+        const int pr = pb + lane / GW, gl = lane % GW;
         int p0 = pr, p1 = me - 1 - pr;
         int ip = p0 == 0 ? 0 : ((p0 - 1 + round) % (me - 1)) + 1;
         int iq = ((p1 - 1 + round) % (me - 1)) + 1;
-        if (ip >= qb || iq >= qb) continue;
+        const bool live = pr < me / 2 && ip < qb && iq < qb;
         if (ip > iq) { int tmp = ip; ip = iq; iq = tmp; }
-        Cx<R>* cp = C + (long long)ip * qa;
-        Cx<R>* cq = C + (long long)iq * qa;
+        Cx<R>* cp = C + (long long)(live ? ip : 0) * qa;
+        Cx<R>* cq = C + (long long)(live ? iq : 0) * qa;
         R al = 0, be = 0;
         Cx<R> ga(0, 0);
-        for (int i = lane; i < qa; i += 32) {
-          al += abs2(cp[i]); be += abs2(cq[i]); cfma_conj(ga, cp[i], cq[i]);
-        }
-        al = warp_sum_r(al); be = warp_sum_r(be); ga = warp_sum(ga);
+        if (live)
+          for (int i = gl; i < qa; i += GW) {
+            al += abs2(cp[i]); be += abs2(cq[i]); cfma_conj(ga, cp[i], cq[i]);
+          }
+        al = group_sum_r(al, GW); be = group_sum_r(be, GW); ga = group_sum(ga, GW);
         const R ag = sqrt(abs2(ga));
-        if (al < Tiny<R>::neg || be < Tiny<R>::neg || !(ag > Tiny<R>::jac * sqrt(al) * sqrt(be))) continue;
-        if (lane == 0) s_rot = 1;
-        const Cx<R> e(ga.re / ag, ga.im / ag);
-        const R z = (be - al) / (R(2) * ag);
-        const R tt = fabs(z) < R(1e18) ? (z >= 0 ? R(1) : R(-1)) / (fabs(z) + sqrt(R(1) + z * z)) : R(0.5) / z;
-        const R cs = R(1) / sqrt(R(1) + tt * tt), sn = tt * cs;
-        const Cx<R> snc = sn * conj(e), sne = sn * e;
-        for (int i = lane; i < qa; i += 32) {
-          const Cx<R> x = cp[i], y = cq[i];
-          cp[i] = cs * x - snc * y;
-          cq[i] = sne * x + cs * y;
-        }
-        Cx<R>* wp = Wm + (long long)ip * g.WCAP;
-        Cx<R>* wq = Wm + (long long)iq * g.WCAP;
-        for (int i = lane; i < qb; i += 32) {
-          const Cx<R> x = wp[i], y = wq[i];
-          wp[i] = cs * x - snc * y;
-          wq[i] = sne * x + cs * y;
+        const bool rot = live && al >= Tiny<R>::neg && be >= Tiny<R>::neg && ag > Tiny<R>::jac * sqrt(al) * sqrt(be);
+        if (rot) {
+          if (gl == 0) s_rot = 1;
+          const Cx<R> e(ga.re / ag, ga.im / ag);
+          const R z = (be - al) / (R(2) * ag);
+          const R tt = fabs(z) < R(1e18) ? (z >= 0 ? R(1) : R(-1)) / (fabs(z) + sqrt(R(1) + z * z)) : R(0.5) / z;
+          const R cs = R(1) / sqrt(R(1) + tt * tt), sn = tt * cs;
+          const Cx<R> snc = sn * conj(e), sne = sn * e;
+          for (int i = gl; i < qa; i += GW) {
+            const Cx<R> x = cp[i], y = cq[i];
+            cp[i] = cs * x - snc * y;
+            cq[i] = sne * x + cs * y;
+          }
+          Cx<R>* wp = Wm + (long long)ip * ldw;
+          Cx<R>* wq = Wm + (long long)iq * ldw;
+          for (int i = gl; i < qb; i += GW) {
+            const Cx<R> x = wp[i], y = wq[i];
+            wp[i] = cs * x - snc * y;
+            wq[i] = sne * x + cs * y;
+          }
         }
       }
       __syncthreads();
@@ -630,37 +684,49 @@ __global__ void svd_jacobi(Geo g, int d, double eps, const Cx<R>* __restrict__ R
   }
   __syncthreads();
   const int keep = s_keep;
-  Cx<R>* Ta = Tx + (long long)a * g.WCAP * g.r_max;   // column-major (ld WCAP)
-  Cx<R>* Tb = Tx + (long long)b * g.WCAP * g.r_max;
+  Cx<R>* Ta = Tx + (long long)a * g.QCAP * g.r_max;   // column-major (ld QCAP)
+  Cx<R>* Tb = Tx + (long long)b * g.QCAP * g.r_max;
   // balanced split: T_a = P_j sigma_j^(1/2), T_b = conj(W_j) sigma_j^(1/2)
   for (int e = threadIdx.x; e < qa * keep; e += blockDim.x) {
     const int i = e % qa, j = e / qa;
     const R f = sqrt(scale / sig[order[j]]);
-    Ta[(long long)j * g.WCAP + i] = f * C[(long long)order[j] * qa + i];
+    Ta[(long long)j * g.QCAP + i] = f * C[(long long)order[j] * qa + i];
   }
   for (int e = threadIdx.x; e < qb * keep; e += blockDim.x) {
     const int i = e % qb, j = e / qb;
     const R f = sqrt(scale * sig[order[j]]);
-    Tb[(long long)j * g.WCAP + i] = f * conj(Wm[(long long)order[j] * g.WCAP + i]);
+    Tb[(long long)j * g.QCAP + i] = f * conj(Wm[(long long)order[j] * ldw + i]);
   }
 }
 
-// Recompression, step 3: F'_u = Q_u T_u (written to the other factor buffer).
+// Recompression, step 3, for the nodes u = list[blockIdx.x]: F'_u = Q_u T_u (T_u itself
+// on the dense path), computed into the node's region of the scratch buffer Fs and copied
+// back into G_F.
 template <typename R>
-__global__ void recompress_apply(Geo g, int d, const Cx<R>* __restrict__ Q, const int* __restrict__ qcols,
-                                 const Cx<R>* __restrict__ Tx, const int* __restrict__ newrank,
-                                 Cx<R>* __restrict__ Fout, int* __restrict__ G_rank) {
-  const int u = (1 << (d + 1)) + blockIdx.x;
+__global__ void recompress_apply(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ qcols,
+                                 const int* __restrict__ qmode, const Cx<R>* __restrict__ Tx,
+                                 const int* __restrict__ newrank, Cx<R>* __restrict__ Fs, int* __restrict__ G_rank) {
+  const int u = g.list[blockIdx.x];
   const int s = g.sz[u], qc = qcols[u], kr = newrank[u];
-  const Cx<R>* Qu = Q + g.gfo[u];
-  const Cx<R>* T = Tx + (long long)u * g.WCAP * g.r_max;
-  Cx<R>* F = Fout + g.gfo[u];
-  for (int e = threadIdx.x; e < s * kr; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    Cx<R> acc(0, 0);
-    for (int l = 0; l < qc; ++l) cfma(acc, Qu[(long long)l * s + i], T[(long long)j * g.WCAP + l]);
-    F[(long long)j * s + i] = acc;
+  const Cx<R>* Qu = G_F + g.gfo[u];
+  const Cx<R>* T = Tx + (long long)u * g.QCAP * g.r_max;
+  Cx<R>* S = Fs + g.gfo[u];
+  if (qmode[u]) {
+    for (int e = threadIdx.x; e < s * kr; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      S[(long long)j * s + i] = T[(long long)j * g.QCAP + i];
+    }
+  } else {
+    for (int e = threadIdx.x; e < s * kr; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      Cx<R> acc(0, 0);
+      for (int l = 0; l < qc; ++l) cfma(acc, Qu[(long long)l * s + i], T[(long long)j * g.QCAP + l]);
+      S[(long long)j * s + i] = acc;
+    }
   }
+  __syncthreads();
+  Cx<R>* F = G_F + g.gfo[u];
+  for (int e = threadIdx.x; e < s * kr; e += blockDim.x) F[e] = S[e];
   if (threadIdx.x == 0) G_rank[u] = kr;
 }
 
@@ -693,45 +759,108 @@ __global__ void store_layer(Geo g, const Cx<R>* __restrict__ G_leaf, const Cx<R>
 
 // ---------------------------------------------------------------------------------------
 struct SetupWork {
-  int KCAP = 0, WCAP = 0;
+  int KCAP = 0, WCAP = 0, QCAP = 0;
   long long gfo_total = 0;   // entries of one G factor buffer
-  std::vector<long long> sfo, gfo;
-  std::vector<int> rowleaf;
+  std::vector<long long> sfo, gfo, qro, rbo;
+  std::vector<int> rowleaf, cap;
+  // node lists of the recompression launches: for depth step d, the nodes of the
+  // non-deferred depths below d (big_nodes[d] .. big_nodes[d+1]) and their left siblings
+  // (big_pairs), then the nodes of the deferred depths (small_*) and all nodes (all_*)
+  std::vector<int> lists;
+  std::vector<int> big_nodes_off, big_pairs_off;
+  int small_nodes_off = 0, small_nodes = 0, small_pairs_off = 0, small_pairs = 0;
+  int all_nodes_off = 0, all_nodes = 0, all_pairs_off = 0, all_pairs = 0;
   long long* d_sfo = nullptr;
   long long* d_gfo = nullptr;
+  long long* d_qro = nullptr;
+  long long* d_rbo = nullptr;
   int* d_rowleaf = nullptr;
+  int* d_cap = nullptr;
+  int* d_lists = nullptr;
   void *S_leaf = nullptr, *S_F = nullptr, *G_leaf = nullptr, *G_F = nullptr, *G_F2 = nullptr;
   void *Y = nullptr, *W = nullptr, *Qr = nullptr, *PQ = nullptr, *M = nullptr, *Rb = nullptr;
   void *Wb = nullptr, *Tx = nullptr;
-  int *S_rank = nullptr, *G_rank = nullptr, *qcols = nullptr, *newrank = nullptr;
+  int *S_rank = nullptr, *G_rank = nullptr, *qcols = nullptr, *qmode = nullptr, *newrank = nullptr;
 };
 
 void hsw_setup_free(hsweep_s* h) {
   if (!h->sw) return;
   SetupWork* w = h->sw;
-  void* ptrs[] = {w->d_sfo, w->d_gfo, w->d_rowleaf, w->S_leaf, w->S_F, w->G_leaf, w->G_F, w->G_F2,
-                  w->Y, w->W, w->Qr, w->PQ, w->M, w->Rb, w->Wb, w->Tx, w->S_rank, w->G_rank,
-                  w->qcols, w->newrank};
+  void* ptrs[] = {w->d_sfo, w->d_gfo, w->d_qro, w->d_rbo, w->d_rowleaf, w->d_cap, w->d_lists, w->S_leaf, w->S_F,
+                  w->G_leaf, w->G_F, w->G_F2, w->Y, w->W, w->Qr, w->PQ, w->M, w->Rb, w->Wb, w->Tx, w->S_rank,
+                  w->G_rank, w->qcols, w->qmode, w->newrank};
   for (void* p : ptrs) hsw_release(h, p);
   delete w;
   h->sw = nullptr;
 }
+
+static int depth_of_host(int v) { int d = 0; while ((2 << d) <= v) ++d; return d; }
 
 static int setup_alloc(hsweep_s* h) {
   SetupWork* w = new (std::nothrow) SetupWork();
   if (!w) return HSWEEP_ERR_OOM;
   h->sw = w;
   const size_t es = h->fac_elem();
-  const int nn = h->nnodes;
+  const int nn = h->nnodes, L = h->L;
   w->KCAP = h->r_max + 1;
   w->WCAP = h->r_max + w->KCAP;
+  // A depth is deferred when the largest core its blocks can reach at the end of a layer,
+  // min(rows, depth x KCAP) (every depth step above appends at most KCAP columns), fits the
+  // Jacobi SVD's shared memory; its blocks are recompressed once per layer.  The other
+  // depths are recompressed after every depth step (at most WCAP columns).
+  const size_t smem_cap = 227 * 1024 - 4096;
+  const int qlim = (int)std::sqrt((double)(smem_cap / es));
+  auto deferred_core = [&](int d) { return std::min(h->tree.maxsz(d), d * w->KCAP); };
+  auto small_depth = [&](int d) { return deferred_core(d) <= qlim; };
+  w->QCAP = w->WCAP;
+  for (int d = 1; d <= L; ++d)
+    if (small_depth(d)) w->QCAP = std::max(w->QCAP, deferred_core(d));
   w->sfo.assign(nn, 0);
   w->gfo.assign(nn, 0);
-  long long so = 0, go = 0;
+  w->qro.assign(nn, 0);
+  w->rbo.assign(nn, 0);
+  w->cap.assign(nn, 0);
+  long long so = 0, go = 0, qo = 0, ro = 0;
   for (int v = 2; v < nn; ++v) {
-    w->sfo[v] = so; so += (long long)h->tree.sz[v] * w->KCAP;
-    w->gfo[v] = go; go += (long long)h->tree.sz[v] * w->WCAP;
+    const int d = depth_of_host(v), sv = h->tree.sz[v];
+    const int cv = small_depth(d) ? d * w->KCAP : w->WCAP;
+    w->cap[v] = cv;
+    w->sfo[v] = so; so += (long long)sv * w->KCAP;
+    w->gfo[v] = go; go += (long long)sv * cv;
+    w->qro[v] = qo; qo += (long long)cv * w->KCAP;
+    w->rbo[v] = ro; ro += (long long)std::min(sv, cv) * cv;
   }
+  // recompression lists
+  w->lists.clear();
+  w->big_nodes_off.assign(L + 1, 0);
+  w->big_pairs_off.assign(L + 1, 0);
+  for (int d = 0; d < L; ++d) {
+    w->big_nodes_off[d] = (int)w->lists.size();
+    for (int v = 2; v < nn; ++v)
+      if (depth_of_host(v) > d && !small_depth(depth_of_host(v))) w->lists.push_back(v);
+  }
+  w->big_nodes_off[L] = (int)w->lists.size();
+  for (int d = 0; d < L; ++d) {
+    w->big_pairs_off[d] = (int)w->lists.size();
+    for (int v = 2; v < nn; v += 2)
+      if (depth_of_host(v) > d && !small_depth(depth_of_host(v))) w->lists.push_back(v);
+  }
+  w->big_pairs_off[L] = (int)w->lists.size();
+  w->small_nodes_off = (int)w->lists.size();
+  for (int v = 2; v < nn; ++v)
+    if (small_depth(depth_of_host(v))) w->lists.push_back(v);
+  w->small_nodes = (int)w->lists.size() - w->small_nodes_off;
+  w->small_pairs_off = (int)w->lists.size();
+  for (int v = 2; v < nn; v += 2)
+    if (small_depth(depth_of_host(v))) w->lists.push_back(v);
+  w->small_pairs = (int)w->lists.size() - w->small_pairs_off;
+  w->all_nodes_off = (int)w->lists.size();
+  for (int v = 2; v < nn; ++v) w->lists.push_back(v);
+  w->all_nodes = nn - 2;
+  w->all_pairs_off = (int)w->lists.size();
+  for (int v = 2; v < nn; v += 2) w->lists.push_back(v);
+  w->all_pairs = (nn - 2) / 2;
+
   w->rowleaf.assign(h->n, 0);
   for (int lam = h->nleaves; lam < 2 * h->nleaves; ++lam)
     for (int i = 0; i < h->tree.sz[lam]; ++i) w->rowleaf[h->tree.lo[lam] + i] = lam;
@@ -741,7 +870,11 @@ static int setup_alloc(hsweep_s* h) {
 #define A(p, bytes) do { rc = hsw_alloc(h, (void**)&(p), (size_t)(bytes)); if (rc) return rc; } while (0)
   A(w->d_sfo, nn * sizeof(long long));
   A(w->d_gfo, nn * sizeof(long long));
+  A(w->d_qro, nn * sizeof(long long));
+  A(w->d_rbo, nn * sizeof(long long));
   A(w->d_rowleaf, h->n * sizeof(int));
+  A(w->d_cap, nn * sizeof(int));
+  A(w->d_lists, std::max<size_t>(1, w->lists.size()) * sizeof(int));
   A(w->S_leaf, lf2 * es);
   A(w->G_leaf, lf2 * es);
   A(w->S_F, std::max(so, 1LL) * es);
@@ -750,21 +883,30 @@ static int setup_alloc(hsweep_s* h) {
   w->gfo_total = std::max(go, 1LL);
   A(w->Y, (long long)h->n * w->KCAP * es);
   A(w->W, (long long)h->n * w->KCAP * es);
-  A(w->Qr, (long long)nn * h->r_max * w->KCAP * es);
+  A(w->Qr, std::max(qo, 1LL) * es);
   A(w->PQ, ntau * 2 * w->KCAP * w->KCAP * es);
   A(w->M, ntau * 4 * w->KCAP * w->KCAP * es);
-  A(w->Rb, (long long)nn * w->WCAP * w->WCAP * es);
-  A(w->Wb, (long long)nn * w->WCAP * w->WCAP * es);
-  A(w->Tx, (long long)nn * w->WCAP * h->r_max * es);
+  A(w->Rb, std::max(ro, 1LL) * es);
+  A(w->Wb, (long long)nn * w->QCAP * w->QCAP * es);
+  A(w->Tx, (long long)nn * w->QCAP * h->r_max * es);
   A(w->S_rank, nn * sizeof(int));
   A(w->G_rank, nn * sizeof(int));
   A(w->qcols, nn * sizeof(int));
+  A(w->qmode, nn * sizeof(int));
   A(w->newrank, nn * sizeof(int));
 #undef A
   HSW_CUDA(cudaMemcpyAsync(w->d_sfo, w->sfo.data(), nn * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   HSW_CUDA(cudaMemcpyAsync(w->d_gfo, w->gfo.data(), nn * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  HSW_CUDA(cudaMemcpyAsync(w->d_qro, w->qro.data(), nn * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  HSW_CUDA(cudaMemcpyAsync(w->d_rbo, w->rbo.data(), nn * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  HSW_CUDA(cudaMemcpyAsync(w->d_cap, w->cap.data(), nn * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   HSW_CUDA(cudaMemcpyAsync(w->d_rowleaf, w->rowleaf.data(), h->n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  if (!w->lists.empty())
+    HSW_CUDA(cudaMemcpyAsync(w->d_lists, w->lists.data(), w->lists.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             h->stream));
   HSW_CUDA(cudaMemsetAsync(w->S_rank, 0, nn * sizeof(int), h->stream));
+  // the host vectors above are read by the asynchronous copies: keep them until the copies ran
+  HSW_CUDA(cudaStreamSynchronize(h->stream));
   return HSWEEP_OK;
 }
 
@@ -774,8 +916,9 @@ static int factor_impl(hsweep_s* h) {
   const size_t es = sizeof(Cx<R>);
   Geo g;
   g.n = h->n; g.L = h->L; g.leaf = h->leaf; g.nnodes = h->nnodes; g.r_max = h->r_max;
-  g.KCAP = w->KCAP; g.WCAP = w->WCAP;
+  g.KCAP = w->KCAP; g.WCAP = w->WCAP; g.QCAP = w->QCAP;
   g.lo = h->d_lo; g.sz = h->d_sz; g.rowleaf = w->d_rowleaf; g.sfo = w->d_sfo; g.gfo = w->d_gfo;
+  g.cap = w->d_cap; g.qro = w->d_qro; g.rbo = w->d_rbo; g.list = w->d_lists;
   cudaStream_t st = h->stream;
   Cx<R>* fac = reinterpret_cast<Cx<R>*>(h->d_fac);
   Cx<R>* S_leaf = (Cx<R>*)w->S_leaf;
@@ -791,10 +934,15 @@ static int factor_impl(hsweep_s* h) {
   Cx<R>* Rb = (Cx<R>*)w->Rb;
   Cx<R>* Wb = (Cx<R>*)w->Wb;
   Cx<R>* Tx = (Cx<R>*)w->Tx;
-  const int L = h->L, nn = h->nnodes, KCAP = w->KCAP, WCAP = w->WCAP;
+  const int L = h->L, nn = h->nnodes, KCAP = w->KCAP, QCAP = w->QCAP;
   const size_t core_smem = (size_t)(2 * KCAP) * (2 * KCAP) * es + 32 * sizeof(R) + (2 * KCAP + 1) * sizeof(int) + 16;
-  const size_t qr_smem = (size_t)(h->tree.maxsz(1) + WCAP) * es + 32 * sizeof(R) + 16;
-  const size_t svd_smem = (size_t)WCAP * WCAP * es + (WCAP + 1) * (sizeof(R) + sizeof(int)) + 64;
+  const size_t qr_smem = (size_t)(h->tree.maxsz(1) + QCAP) * es + 32 * sizeof(R) + 16;
+  // the Jacobi SVD's shared memory: C and, where it fits, the rotations W (up to 2 QCAP^2
+  // entries; for large cores W stays in global memory)
+  const size_t svd_tail = (size_t)(QCAP + 1) * sizeof(R) + (size_t)QCAP * sizeof(int) + 64;
+  // (1 KB of the 227 KB per block stays free for the kernel's static shared variables)
+  const int svd_entries = (int)std::min<size_t>((size_t)2 * QCAP * QCAP, (226 * 1024 - svd_tail) / es);
+  const size_t svd_smem = (size_t)svd_entries * es + svd_tail;
   // one shared-memory carveout for every kernel of the layer loop, so that consecutive
   // launches do not reconfigure the SMs' L1/shared split
   {
@@ -809,15 +957,31 @@ static int factor_impl(hsweep_s* h) {
   HSW_CUDA(cudaFuncSetAttribute(core_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem));
   HSW_CUDA(cudaFuncSetAttribute(qr_cgs2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem));
   HSW_CUDA(cudaFuncSetAttribute(svd_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)svd_smem));
-  if (core_smem > 227 * 1024 || qr_smem > 227 * 1024 || svd_smem > 227 * 1024) return HSWEEP_ERR_ARG;
+  if (core_smem > 227 * 1024 || qr_smem > 227 * 1024 || svd_smem > 227 * 1024 || svd_entries < QCAP * QCAP)
+    return HSWEEP_ERR_ARG;
+
+  // QR (or the dense path), SVD of the cores and the new factors, for nn_list nodes whose
+  // list starts at node_off and their np_list left siblings at pair_off
+  auto recompress = [&](int node_off, int nn_list, int pair_off, int np_list) {
+    if (nn_list <= 0) return;
+    Geo gl = g;
+    gl.list = w->d_lists + node_off;
+    qr_cgs2<R><<<nn_list, 1024, qr_smem, st>>>(gl, G_F, w->G_rank, Rb, w->qcols, w->qmode);
+    Geo gp = g;
+    gp.list = w->d_lists + pair_off;
+    svd_jacobi<R><<<np_list, 1024, svd_smem, st>>>(gp, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx, w->newrank,
+                                                   svd_entries);
+    recompress_apply<R><<<nn_list, kBlk, 0, st>>>(gl, G_F, w->qcols, w->qmode, Tx, w->newrank, G_F2, w->G_rank);
+    h->nlaunch += 3;
+  };
 
   for (int m = 0; m < h->n; ++m) {
     const Cx<R>* Tprev = m > 0 ? fac + (long long)(m - 1) * h->layer_stride : nullptr;
     const int* rprev = m > 0 ? h->d_rank + (long long)(m - 1) * nn : nullptr;
-    schur_leaves<R><<<h->nleaves, 64, 0, st>>>(g, m, h->d_diag, h->d_east, h->d_north, Tprev, S_leaf);
+    schur_leaves<R><<<h->nleaves, 64, 0, st>>>(g, m, h->d_diag_m, h->d_east_m, h->d_north_m, Tprev, S_leaf);
     h->nlaunch += 1;
     if (nn > 2) {
-      schur_factors<R><<<nn - 2, kBlk, 0, st>>>(g, m, h->d_east, h->d_north, Tprev, h->d_off, rprev, S_F,
+      schur_factors<R><<<nn - 2, kBlk, 0, st>>>(g, m, h->d_east_m, h->d_north_m, Tprev, h->d_off, rprev, S_F,
                                                  w->S_rank);
       h->nlaunch += 1;
     }
@@ -843,15 +1007,12 @@ static int factor_impl(hsweep_s* h) {
       h->nlaunch += 1;
       woodbury_append<R><<<n_below1, kBlk, 0, st>>>(g, d, w->S_rank, Y, Wv, G_F, w->G_rank, G_leaf);
       h->nlaunch += 1;
-      qr_cgs2<R><<<n_below1, 1024, qr_smem, st>>>(g, d, G_F, w->G_rank, Rb, w->qcols);
-      h->nlaunch += 1;
-      svd_jacobi<R><<<n_below1 / 2, 1024, svd_smem, st>>>(g, d, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx,
-                                                         w->newrank);
-      h->nlaunch += 1;
-      recompress_apply<R><<<n_below1, kBlk, 0, st>>>(g, d, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);
-      h->nlaunch += 1;
-      std::swap(G_F, G_F2);
+      // the blocks of the non-deferred depths that this depth step changed
+      recompress(w->big_nodes_off[d], w->big_nodes_off[d + 1] - w->big_nodes_off[d], w->big_pairs_off[d],
+                 w->big_pairs_off[d + 1] - w->big_pairs_off[d]);
     }
+    // the blocks of the deferred depths, once per layer, in their final form
+    recompress(w->small_nodes_off, w->small_nodes, w->small_pairs_off, w->small_pairs);
     if (h->strong_R > 0) {
       // strongly admissible T~_m (strong.cu), then one recompression of every sibling pair:
       // the expanded layout can carry more columns than a block has rows (small blocks,
@@ -860,12 +1021,7 @@ static int factor_impl(hsweep_s* h) {
       int rc = hsw_strong_project(h, m, G_F, w->G_rank, G_F2, w->d_gfo, w->gfo_total);
       if (rc) return rc;
       std::swap(G_F, G_F2);
-      const int n_all = nn - 2;
-      qr_cgs2<R><<<n_all, 1024, qr_smem, st>>>(g, 0, G_F, w->G_rank, Rb, w->qcols);
-      svd_jacobi<R><<<n_all / 2, 1024, svd_smem, st>>>(g, 0, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx, w->newrank);
-      recompress_apply<R><<<n_all, kBlk, 0, st>>>(g, 0, G_F, w->qcols, Tx, w->newrank, G_F2, w->G_rank);
-      h->nlaunch += 3;
-      std::swap(G_F, G_F2);
+      recompress(w->all_nodes_off, w->all_nodes, w->all_pairs_off, w->all_pairs);
     }
     store_layer<R><<<nn, kBlk, 0, st>>>(g, G_leaf, G_F, w->G_rank, fac + (long long)m * h->layer_stride,
                                         h->d_off, h->d_rank + (long long)m * nn);

@@ -40,7 +40,8 @@ namespace {
 
 using namespace tma;
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 512;              // threads of the one-CTA-per-SM variant
+constexpr int kThreads2 = 256;             // threads of the two-CTAs-per-SM variant
 constexpr int kKS = 8;                      // expansion: lanes (column slices) per row
 constexpr int kKW = 8;                      // reduction: column lanes per warp-item
 // update pairs (row, right-hand side) per thread: slab rows x G <= kThreads * upt(G)
@@ -261,15 +262,17 @@ __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const C
   }
 }
 
-template <typename R, int G, int TC>
-__global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) {
+// NT threads per CTA: 512 with one CTA per SM, or 256 with two CTAs per SM (the same
+// registers per thread; one CTA's barrier waits and latencies are covered by the other's)
+template <typename R, int G, int TC, int NT>
+__global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<R> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   using M = Mac<R>;
   using T = Tagged<R>;
   constexpr int GS = vstride<R>(G);
   constexpr int kUPT = upt(G);
-  constexpr bool kTC = TC > 0 && std::is_same<R, float>::value;    // reductions on tensor cores
-  constexpr bool kTCE = TC > 1 && std::is_same<R, float>::value;   // and the expansion
+  constexpr bool kTC = TC > 0 && std::is_same<R, float>::value && NT == kThreads;   // reductions on tensor cores
+  constexpr bool kTCE = TC > 1 && std::is_same<R, float>::value && NT == kThreads;  // and the expansion
   constexpr bool tc = kTC;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n, L = a.L, dC = a.dC, nl = a.nl, lf = a.leaf, SM = a.slab_max;
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
   Cx<R>* qanc = reinterpret_cast<Cx<R>*>(sm + a.o_qanc);
   Cx<R>* qloc = reinterpret_cast<Cx<R>*>(sm + a.o_qloc);
 
-  for (int v = tid; v < a.nnodes; v += kThreads) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
+  for (int v = tid; v < a.nnodes; v += NT) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
   __syncthreads();
   const int lo_c = s_lo[vc], ns = s_sz[vc];
   if (tid == 0) {
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     mbar_init(&mbar[1], 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < ns; i += kThreads) {
+  for (int i = tid; i < ns; i += NT) {
     int v = vc;
     for (int d = dC; d < L; ++d) v = 2 * v + ((lo_c + i) >= s_lo[2 * v + 1] ? 1 : 0);
     s_leafnode[i] = v;
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     auto rank_at = [&](int lam, int d) {
       return d <= dC ? trk[d - 1] : trk[dC + (1 << (d - dC)) - 2 + ((lam >> (L - d)) - (vc << (d - dC)))];
     };
-    for (int e = tid; e < ns * L1; e += kThreads) {
+    for (int e = tid; e < ns * L1; e += NT) {
       const int i = e % ns, d = e / ns;
       const int lam = s_leafnode[i];
       const int j = lam - lam0;
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
       }
       rowoff[d * SM + i] = o;
     }
-    for (int e = tid; e < nl * L1; e += kThreads) {
+    for (int e = tid; e < nl * L1; e += NT) {
       const int j = e / L1, d = e % L1;
       const int lam = lam0 + j;
       int r, vo = 0;
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     // y[i][g] and then writes x_next[i][g] in the same thread
     Cx<R>* ybuf = xn;
     if (s == 0) {     // a new group: x = r restricted to layer 0 and the slab's rows
-      for (int it = tid; it < ns * G; it += kThreads) {
+      for (int it = tid; it < ns * G; it += NT) {
         const int i = it / G, g = it % G;
         Cx<R> v(0, 0);
         if (g < gcount) v = cvt<R>(a.r[(long long)(g0 + g) * a.N + lo_c + i]);
@@ -601,14 +604,14 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
       const int tot = dC * rg;
       const long long cstride = (long long)dC * rg;
       const typename T::W* xb = a.xch + ((long long)slot * a.nteams + team) * a.C * cstride;
-      for (int base = tid; base < tot; base += GJ * kThreads) {
+      for (int base = tid; base < tot; base += GJ * NT) {
         typename T::W vals[GJ][8];
         const typename T::W* src[GJ];
         int span[GJ];
         bool use[GJ];
 #pragma unroll
         for (int j = 0; j < GJ; ++j) {
-          const int it = base + j * kThreads;
+          const int it = base + j * NT;
           const int d = it < tot ? it / rg + 1 : 1;
           const int kg = it - (d - 1) * rg;
           span[j] = 1 << (dC - d);
@@ -642,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
         }
 #pragma unroll
         for (int j = 0; j < GJ; ++j) {
-          const int it = base + j * kThreads;
+          const int it = base + j * NT;
           if (it >= tot) continue;
           Cx<R> acc(0, 0);
           if (use[j]) {
@@ -743,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     } else {
       // lane = (row i, column slice ks), all depths on CUDA cores
       const int nitems = ns * kKS;
-      for (int item = tid; item < ((nitems + 31) & ~31); item += kThreads) {
+      for (int item = tid; item < ((nitems + 31) & ~31); item += NT) {
         const bool live = item < nitems;
         const int ks = item % kKS;
         const int i = live ? item / kKS : 0;
@@ -780,7 +783,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     Cx<R> pw[kUPT];
 #pragma unroll
     for (int u = 0; u < kUPT; ++u) {
-      const int p = tid + u * kThreads;
+      const int p = tid + u * NT;
       pcpl[u] = c128(0.0, 0.0);
       pin[u] = c128(0.0, 0.0);
       pw[u] = Cx<R>(0, 0);
@@ -800,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_team_kernel(TeamArgs<R> a) 
     //         step's row offsets ---------------------------------------------------------
 #pragma unroll
     for (int u = 0; u < kUPT; ++u) {
-      const int p = tid + u * kThreads;
+      const int p = tid + u * NT;
       if (p < ns * G) {
         const int i = p % ns, g = p / ns;
         const bool valid = g < gcount;
@@ -850,20 +853,21 @@ struct TeamConfig {
   bool ok;
   int dC, C, G, nteams;
   size_t smem;
+  int nt;              // threads per CTA (kThreads or kThreads2)
 };
 
 static int ilog2t(int x) { int l = 0; while ((1 << (l + 1)) <= x) ++l; return l; }
 
 // shared-memory plan for (dC, G); returns total bytes (0 if the layout is not supported)
 template <typename R>
-static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a) {
+static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a, int nt = kThreads) {
   const size_t es = sizeof(Cx<R>);
   const int L = h->L;
   const int nl = 1 << (L - dC);
   const int slab_max = h->tree.maxsz(dC);
   const int rcap = std::max(1, h->rank_max);
   const int GS = vstride<R>(G);
-  if (L > 14 || (long long)slab_max * G > (long long)upt(G) * kThreads || h->leaf > 8) return 0;
+  if (L > 14 || (long long)slab_max * G > (long long)upt(G) * nt || h->leaf > 8) return 0;
   auto al = [](size_t x, size_t b) { return (x + b - 1) / b * b; };
   size_t o = 0;
   const size_t stage = al((size_t)h->slab_bytes_max[dC], 128);
@@ -897,62 +901,77 @@ static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a) {
   return o;
 }
 
-template <typename R, int G>
+template <typename R, int G, int NT>
 static int resident_ctas(const hsweep_s* h, size_t smem) {
-  auto kern = sweep_team_kernel<R, G, 0>;
+  auto kern = sweep_team_kernel<R, G, 0, NT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return per_sm * h->num_sms;
 }
 
-template <typename R>
-static int resident_for(const hsweep_s* h, int G, size_t smem) {
+template <typename R, int NT>
+static int resident_for_nt(const hsweep_s* h, int G, size_t smem) {
   switch (G) {
-    case 1: return resident_ctas<R, 1>(h, smem);
-    case 2: return resident_ctas<R, 2>(h, smem);
-    case 4: return resident_ctas<R, 4>(h, smem);
-    case 5: return resident_ctas<R, 5>(h, smem);
-    default: return resident_ctas<R, 8>(h, smem);
+    case 1: return resident_ctas<R, 1, NT>(h, smem);
+    case 2: return resident_ctas<R, 2, NT>(h, smem);
+    case 4: return resident_ctas<R, 4, NT>(h, smem);
+    case 5: return resident_ctas<R, 5, NT>(h, smem);
+    default: return resident_ctas<R, 8, NT>(h, smem);
   }
 }
 
-// Team size C and right-hand sides per team G: the fewest rounds of 2n-1 dependent
-// steps, a step costing a fixed latency (exchange through L2, barriers) plus work that grows
-// with the slab's rows times G.
+template <typename R>
+static int resident_for(const hsweep_s* h, int G, size_t smem, int nt) {
+  return nt == kThreads2 ? resident_for_nt<R, kThreads2>(h, G, smem) : resident_for_nt<R, kThreads>(h, G, smem);
+}
+
+// Team size C, right-hand sides per team G and threads per CTA: the fewest rounds of 2n-1
+// dependent steps, a step costing a fixed latency (exchange through L2, barriers, growing
+// with the team's depth) plus work that grows with the slab's rows times G per thread.  Two
+// CTAs of 256 threads on one SM cover each other's barrier waits and latencies: their work
+// term is weighted by kShare2 (measured, the bench's component timings).
+constexpr double kShare2 = 1.5;
+
 template <typename R>
 static TeamConfig choose_team_uncached(const hsweep_s* h, int nrhs) {
   TeamConfig best{};
   best.ok = false;
   double best_cost = 1e300;
   const size_t cap = 227 * 1024;
-  const int C_pref = h->opt.team, G_pref = h->opt.groups;
-  for (int C = 1; C <= h->nleaves && C <= h->num_sms; C *= 2) {
+  const int C_pref = h->opt.team, G_pref = h->opt.groups, T_pref = h->opt.team_threads;
+  for (int C = 1; C <= h->nleaves && C <= 2 * h->num_sms; C *= 2) {
     if (C_pref > 0 && C != (1 << ilog2t(C_pref))) continue;
     const int dC = ilog2t(C);
-    for (int G : {8, 5, 4, 2, 1}) {
-      if (G_pref > 0 && G != G_pref) continue;
-      TeamArgs<R> a;
-      const size_t smem = plan_team<R>(h, dC, G, a);
-      if (smem == 0 || smem > cap) continue;
-      const int resident = resident_for<R>(h, G, smem);
-      const int teams_cap = std::min(resident, 1024) / C;
-      if (teams_cap < 1) continue;
-      const int ngroups = (nrhs + G - 1) / G;
-      const int teams = std::min(ngroups, teams_cap);
-      const int rounds = (ngroups + teams - 1) / teams;
-      const double es = (double)sizeof(Cx<R>) / 8.0;
-      const double step = 2.5 + 0.012 * es * a.slab_max * G + 0.4 * dC + 0.01 * C;
-      const double cost = rounds * step;
-      if (cost < best_cost - 1e-9) {
-        best_cost = cost;
-        best = TeamConfig{true, dC, C, G, teams, smem};
+    for (int nt : {kThreads, kThreads2}) {
+      if (T_pref > 0 && nt != T_pref) continue;
+      for (int G : {8, 5, 4, 2, 1}) {
+        if (G_pref > 0 && G != G_pref) continue;
+        TeamArgs<R> a;
+        const size_t smem = plan_team<R>(h, dC, G, a, nt);
+        if (smem == 0 || smem > cap) continue;
+        const int resident = resident_for<R>(h, G, smem, nt);
+        const int teams_cap = std::min(resident, 1024) / C;
+        if (teams_cap < 1) continue;
+        // the two-CTA variant only where two CTAs per SM are resident
+        if (nt == kThreads2 && resident < 2 * h->num_sms) continue;
+        const int ngroups = (nrhs + G - 1) / G;
+        const int teams = std::min(ngroups, teams_cap);
+        const int rounds = (ngroups + teams - 1) / teams;
+        const double es = (double)sizeof(Cx<R>) / 8.0;
+        const double work = 0.012 * es * a.slab_max * G * ((double)kThreads / nt) * (nt == kThreads2 ? kShare2 : 1.0);
+        const double step = 2.5 + work + 0.4 * dC + 0.01 * C;
+        const double cost = rounds * step;
+        if (cost < best_cost - 1e-9) {
+          best_cost = cost;
+          best = TeamConfig{true, dC, C, G, teams, smem, nt};
+        }
       }
     }
   }
@@ -964,24 +983,24 @@ static TeamConfig choose_team_uncached(const hsweep_s* h, int nrhs) {
 template <typename R>
 static TeamConfig choose_team(hsweep_s* h, int nrhs) {
   for (const auto& e : h->team_plans)
-    if (e[0] == nrhs) return TeamConfig{e[1] != 0, (int)e[2], (int)e[3], (int)e[4], (int)e[5], (size_t)e[6]};
+    if (e[0] == nrhs) return TeamConfig{e[1] != 0, (int)e[2], (int)e[3], (int)e[4], (int)e[5], (size_t)e[6], (int)e[7]};
   const TeamConfig c = choose_team_uncached<R>(h, nrhs);
   if (h->team_plans.size() >= 64) h->team_plans.erase(h->team_plans.begin());
-  h->team_plans.push_back({nrhs, c.ok ? 1 : 0, c.dC, c.C, c.G, c.nteams, (long long)c.smem});
+  h->team_plans.push_back({nrhs, c.ok ? 1 : 0, c.dC, c.C, c.G, c.nteams, (long long)c.smem, c.nt});
   return c;
 }
 
-template <typename R, int G>
+template <typename R, int G, int NT>
 static int launch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
-  auto kern = sweep_team_kernel<R, G, 0>;
-  if constexpr (sizeof(R) == 4) {
-    if (a.tc == 1) kern = sweep_team_kernel<R, G, 1>;
-    if (a.tc == 2) kern = sweep_team_kernel<R, G, 2>;
+  auto kern = sweep_team_kernel<R, G, 0, NT>;
+  if constexpr (sizeof(R) == 4 && NT == kThreads) {
+    if (a.tc == 1) kern = sweep_team_kernel<R, G, 1, NT>;
+    if (a.tc == 2) kern = sweep_team_kernel<R, G, 2, NT>;
   }
   HSW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
-  lc.blockDim = dim3(kThreads);
+  lc.blockDim = dim3(NT);
   lc.gridDim = dim3(cfg.C * cfg.nteams);
   lc.dynamicSmemBytes = cfg.smem;
   lc.stream = h->stream;
@@ -1008,12 +1027,21 @@ static int launch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
 
 template <typename R>
 static int dispatch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
+  if (cfg.nt == kThreads2) {
+    switch (cfg.G) {
+      case 1: return launch_team<R, 1, kThreads2>(h, cfg, a);
+      case 2: return launch_team<R, 2, kThreads2>(h, cfg, a);
+      case 4: return launch_team<R, 4, kThreads2>(h, cfg, a);
+      case 5: return launch_team<R, 5, kThreads2>(h, cfg, a);
+      default: return launch_team<R, 8, kThreads2>(h, cfg, a);
+    }
+  }
   switch (cfg.G) {
-    case 1: return launch_team<R, 1>(h, cfg, a);
-    case 2: return launch_team<R, 2>(h, cfg, a);
-    case 4: return launch_team<R, 4>(h, cfg, a);
-    case 5: return launch_team<R, 5>(h, cfg, a);
-    default: return launch_team<R, 8>(h, cfg, a);
+    case 1: return launch_team<R, 1, kThreads>(h, cfg, a);
+    case 2: return launch_team<R, 2, kThreads>(h, cfg, a);
+    case 4: return launch_team<R, 4, kThreads>(h, cfg, a);
+    case 5: return launch_team<R, 5, kThreads>(h, cfg, a);
+    default: return launch_team<R, 8, kThreads>(h, cfg, a);
   }
 }
 
@@ -1061,14 +1089,14 @@ static int apply_team_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
     xptr = h->d_xch;
   }
   TeamArgs<R> a;
-  plan_team<R>(h, cfg.dC, cfg.G, a);
+  plan_team<R>(h, cfg.dC, cfg.G, a, cfg.nt);
   a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.nnodes = h->nnodes; a.dC = cfg.dC; a.C = cfg.C;
   a.nteams = cfg.nteams; a.nrhs = nrhs; a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
   a.N = h->N; a.pack_stride = h->pack_stride;
-  a.tc = (sizeof(R) == 4 && a.slab_max <= 64) ? h->opt.sweep_tc : 0;
+  a.tc = (sizeof(R) == 4 && a.slab_max <= 64 && cfg.nt == kThreads) ? h->opt.sweep_tc : 0;
   a.lo = h->d_lo; a.sz = h->d_sz; a.rank = h->d_rank; a.recoff = h->d_recoff;
   a.pack = reinterpret_cast<const Cx<R>*>(h->d_pack);
-  a.north = h->d_north; a.r = r; a.z = z;
+  a.north = h->d_north_m; a.r = r; a.z = z;
   a.w = reinterpret_cast<Cx<R>*>(wptr);
   a.xch = reinterpret_cast<typename Tagged<R>::W*>(xptr);
   a.status = h->d_status;
@@ -1104,7 +1132,7 @@ int hsw_team_plan(hsweep_s* h, int nrhs, long long* out) {
   TeamConfig cfg{};
   if (team_usable(h)) cfg = h->prec == HSWEEP_FP64 ? choose_team<double>(h, nrhs) : choose_team<float>(h, nrhs);
   if (!cfg.ok) return 0;
-  out[0] = 2; out[1] = cfg.C; out[2] = cfg.G; out[3] = cfg.nteams; out[4] = 0;
+  out[0] = 2; out[1] = cfg.C; out[2] = cfg.G; out[3] = cfg.nteams; out[4] = cfg.nt;
   out[5] = (long long)cfg.smem; out[6] = h->slab_bytes_max[cfg.dC]; out[7] = kKS;
   return 1;
 }

@@ -138,6 +138,41 @@ def test_team_sweep_matches_basic_sweep_and_exact(hs, n, prec, nrhs, team):
     h2.free()
 
 
+@pytest.mark.parametrize("n,prec,nrhs,team", [(255, 0, 8, 16), (255, 1, 16, 16), (511, 1, 64, 32), (127, 0, 3, 8),
+                                              (511, 0, 9, 32)])
+def test_two_ctas_per_sm_team_sweep_matches_basic_sweep_and_exact(hs, n, prec, nrhs, team):
+    # the 256-thread variant of the team kernel (two CTAs per SM, half the slab rows per
+    # CTA) against the basic kernel on the same factors and the exact sweep of the
+    # exported layers
+    c, omega, pml = _problem(n, 6)
+    disc = Discretization(c, omega, pml)
+    h1 = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6,
+                         hs.default_opts(precision=prec, team=team, team_threads=256))
+    plan = h1.sweep_plan(nrhs)
+    assert plan["tma"] == 2 and plan["grid_or_threads"] == 256 and plan["team_ctas"] == team, plan
+    R = torch.randn(nrhs, n * n, dtype=torch.complex128, device="cuda")
+    Z1 = h1.apply(R)
+    Z1b = h1.apply(R)
+    h2 = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6,
+                         hs.default_opts(precision=prec, sweep_kernel=1))
+    Z2 = h2.apply(R)
+    torch.cuda.synchronize()
+    assert h1.status()[0] == 0 and h2.status()[0] == 0
+    assert torch.equal(Z1, Z1b)                  # deterministic
+    tol = 1e-12 if prec == 0 else 2e-5
+    err = (torch.linalg.norm(Z1 - Z2) / torch.linalg.norm(Z2)).item()
+    assert err < tol, err
+    T = []
+    for m in range(n):
+        lv, fac, rk = h1.export_layer(m)
+        T.append(layer_to_dense(n, 8, 48, lv, fac, rk))
+    ref = solve_exact(disc, T, R[nrhs - 1].cpu().numpy())
+    e2 = np.linalg.norm(Z1[nrhs - 1].cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert e2 < tol, e2
+    h1.free()
+    h2.free()
+
+
 @pytest.mark.parametrize("n,nrhs,groups", [(255, 8, 0), (255, 5, 5), (255, 16, 0), (127, 3, 2)])
 def test_tensor_core_ancestor_terms_match_cuda_core_path(hs, n, nrhs, groups):
     # complex64 team sweep: ancestor contractions on tensor cores (TF32 in three parts)
@@ -164,3 +199,21 @@ def test_tensor_core_ancestor_terms_match_cuda_core_path(hs, n, nrhs, groups):
     ref = solve_exact(disc, T, R[nrhs - 1].cpu().numpy())
     e2 = np.linalg.norm(Z[1][nrhs - 1].cpu().numpy() - ref) / np.linalg.norm(ref)
     assert e2 < 2e-5, e2
+
+
+def test_mixed_apply_departs_from_a_linear_map_by_far_less_than_the_solve_assumes(hs):
+    # the mixed solve ends its refinement on the inner GMRES estimate once the complex64
+    # sweep's departure from linearity (assumed below 1e-5 relative) cannot matter; the
+    # departure measured on the n = 511 lens workload must be well below that bound
+    w = synth.workload("n511_lens")
+    n = w["n"]
+    h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], w["eps_H"],
+                        hs.default_opts(precision=hs.MIXED))
+    g = torch.Generator(device="cpu").manual_seed(5)
+    X = torch.randn(4, n * n, dtype=torch.complex128, generator=g).cuda()
+    Y = 1e-3 * torch.randn(4, n * n, dtype=torch.complex128, generator=g).cuda()
+    MX, MY, MXY = h.apply(X), h.apply(Y), h.apply(X + Y)
+    torch.cuda.synchronize()
+    h.free()
+    dev = torch.linalg.norm(MXY - MX - MY, dim=1) / (torch.linalg.norm(MX, dim=1) + torch.linalg.norm(MY, dim=1))
+    assert dev.max().item() < 2e-6, dev
