@@ -357,6 +357,9 @@ def main():
     ap.add_argument("--setup-only", action="store_true", help="time only the setup sweep (Algorithm 2.5)")
     ap.add_argument("--team", type=int, default=0, help="with --apply-only: CTAs per sweep team (0 = automatic)")
     ap.add_argument("--groups", type=int, default=0, help="with --apply-only: right-hand sides per team (0 = automatic)")
+    ap.add_argument("--core-kernel", type=int, default=0,
+                    help="with --setup-only / --apply-only: recompression cores on the autotuned kernel (0), "
+                         "CUDA cores (1) or tensor cores (2)")
     ap.add_argument("--team-threads", type=int, default=0,
                     help="with --apply-only: threads per CTA of the team sweep (512, 256; 0 = automatic)")
     ap.add_argument("--sweep-tc", type=int, default=0, help="with --apply-only: ancestor contractions on tensor cores")
@@ -804,11 +807,12 @@ def run_parts(args):
     t0 = time.perf_counter()
     h = hs.hsweep_setup(c_d, w["omega"], w["pml"], w["eps_H"],
                         hs.default_opts(precision=prec, team=args.team, groups=args.groups, sweep_tc=args.sweep_tc,
-                                        strong_rank=args.strong_rank, team_threads=args.team_threads))
+                                        strong_rank=args.strong_rank, team_threads=args.team_threads,
+                                        core_kernel=args.core_kernel))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     out = {"workload": args.workload, "n": n, "precision": "fp64" if args.fp64 else "mixed", "setup_s": setup_s,
-           "strong_rank": args.strong_rank, "info": h.info()}
+           "strong_rank": args.strong_rank, "info": h.info(), "setup_tuning": h.setup_tuning()}
     if args.apply_only:
         nrhs = args.apply_only
         F = w["f"].reshape(w["f"].shape[0], -1)

@@ -114,6 +114,9 @@ typedef struct {
   unsigned rsvd_seed; /* key of the Philox4x32-10 generator of those test vectors (default 0) */
   int team_threads;  /* threads per CTA of the team sweep: 512 (one CTA per SM), 256 (two CTAs
                         per SM, half the rows per CTA) or 0 (default: the launch plan chooses) */
+  int core_kernel;   /* recompression cores C = R_a R_b^t (hsweep_setup_tuning): 0 (default) the
+                        setup's autotuned choice, 1 CUDA cores, 2 tensor cores (HSWEEP_MIXED;
+                        HSWEEP_FP64 always uses CUDA cores) */
   int krylov_lowp;   /* HSWEEP_MIXED only.  0 (default): every operation of the inner GMRES
                         (Gram-Schmidt dots and updates, norms, scalings, the product with A)
                         computes in FP64.  1: those operations compute in FP32 on the
@@ -304,6 +307,17 @@ HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
  * out[7] column slices per row in the expansion (0 for the basic kernel).
  */
 HSWEEP_API int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8);
+
+/*
+ * The setup's autotuning of the recompression cores C = R_a R_b^t (Section 2.3, "Matrix
+ * addition": the small matrix whose SVD truncates a block), diagnostics: in complex64 the
+ * setup times, on its middle layer, a CUDA-core kernel and a tensor-core kernel (TF32
+ * operands in three parts, FP32 accumulation) on the first launch of each kind and keeps
+ * the faster.  out6 (host): [0] kind 0 (recompression after a depth step) and [1] kind 1
+ * (once per layer): -1 not tuned (complex128, or no launch of that kind), 0 CUDA cores,
+ * 1 tensor cores; [2], [3] the two candidates' times (ms) for kind 0; [4], [5] for kind 1.
+ */
+HSWEEP_API int hsweep_setup_tuning(hsweep_t h, double* out6);
 
 /*
  * z = M r exactly as hsweep_apply, for callers that must not allocate device memory

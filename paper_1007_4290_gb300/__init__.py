@@ -27,7 +27,7 @@ EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_appl
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
             "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan", "hsweep_philox4x32_10",
-            "hsweep_rsvd_normals", "hsweep_strong_plan"]
+            "hsweep_rsvd_normals", "hsweep_strong_plan", "hsweep_setup_tuning"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -38,7 +38,7 @@ class hsweep_opts(ctypes.Structure):
                 ("sweep_kernel", ctypes.c_int), ("sweep_tc", ctypes.c_int),
                 ("sweep_dir", ctypes.c_int), ("pml_sides", ctypes.c_int),
                 ("strong_rank", ctypes.c_int), ("rsvd_seed", ctypes.c_uint),
-                ("team_threads", ctypes.c_int), ("krylov_lowp", ctypes.c_int)]
+                ("team_threads", ctypes.c_int), ("core_kernel", ctypes.c_int), ("krylov_lowp", ctypes.c_int)]
 
 
 class HSweepError(RuntimeError):
@@ -72,6 +72,7 @@ def load_library(path=LIB_PATH):
         "hsweep_stats": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]),
         "hsweep_apply_noalloc": (I, [P, P, P, I]),
         "hsweep_sweep_plan": (I, [P, I, ctypes.POINTER(LL)]),
+        "hsweep_setup_tuning": (I, [P, ctypes.POINTER(D)]),
         "hsweep_philox4x32_10": (I, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                      ctypes.POINTER(ctypes.c_uint32)]),
         "hsweep_rsvd_normals": (I, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, I, I, P]),
@@ -203,6 +204,15 @@ class Handle:
         keys = ["tma", "team_ctas", "rhs_per_team", "teams", "grid_or_threads", "smem", "record_bytes_max",
                 "leaves_per_chunk"]
         return dict(zip(keys, list(out)))
+
+    def setup_tuning(self):
+        """The setup's choice of core-product kernel per kind of recompression launch
+        (hsweep_setup_tuning): {"after_depth": mode, "per_layer": mode, "ms": [[cc, tc], [cc, tc]]},
+        mode -1 not tuned, 0 CUDA cores, 1 tensor cores."""
+        out = (ctypes.c_double * 6)()
+        _check(_lib.hsweep_setup_tuning(self.raw, out), "hsweep_setup_tuning")
+        v = list(out)
+        return {"after_depth": int(v[0]), "per_layer": int(v[1]), "ms": [[v[2], v[3]], [v[4], v[5]]]}
 
     def layer_ranks(self, m):
         L = self.info()["L"]

@@ -71,6 +71,7 @@ extern "C" int hsweep_default_opts(hsweep_opts* o) {
   o->strong_rank = 0;
   o->rsvd_seed = 0;
   o->team_threads = 0;
+  o->core_kernel = 0;
   o->krylov_lowp = 0;
   return HSWEEP_OK;
 }
@@ -110,7 +111,8 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
       (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15 ||
       opt.strong_rank < 0 || opt.strong_rank > 8 || opt.krylov_lowp < 0 || opt.krylov_lowp > 1 ||
-      (opt.team_threads != 0 && opt.team_threads != 256 && opt.team_threads != 512))
+      (opt.team_threads != 0 && opt.team_threads != 256 && opt.team_threads != 512) ||
+      opt.core_kernel < 0 || opt.core_kernel > 2)
     return HSWEEP_ERR_ARG;
   hsweep_s* h = new (std::nothrow) hsweep_s();
   if (!h) return HSWEEP_ERR_OOM;
@@ -446,6 +448,16 @@ extern "C" int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
     h->nlaunch = 0;
     for (auto& pr : h->ev_sweep) { h->ev_free.push_back(pr.first); h->ev_free.push_back(pr.second); }
     h->ev_sweep.clear();
+  }
+  return HSWEEP_OK;
+}
+
+extern "C" int hsweep_setup_tuning(hsweep_t h, double* out6) {
+  if (!h || !out6) return HSWEEP_ERR_ARG;
+  for (int k = 0; k < 2; ++k) {
+    out6[k] = h->core_mode[k];
+    out6[2 + 2 * k] = h->core_ms[k][0];
+    out6[3 + 2 * k] = h->core_ms[k][1];
   }
   return HSWEEP_OK;
 }

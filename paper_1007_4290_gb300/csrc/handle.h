@@ -101,6 +101,12 @@ struct hsweep_s {
 
   std::vector<void*> allocs;   // every device allocation owned by the handle
 
+  // setup autotuning of the recompression's core products (setup.cu): per kind of launch
+  // (0: after a depth step, 1: once per layer) the kernel kept (-1 not tuned, 0 CUDA cores,
+  // 1 tensor cores) and the two candidates' times in milliseconds
+  int core_mode[2] = {-1, -1};
+  float core_ms[2][2] = {{0, 0}, {0, 0}};
+
   // device address of the library's fixed scratch array for hsweep_apply_noalloc, looked
   // up on the handle's device when the handle is created (noalloc.cu); null if that failed
   void* noalloc_scratch = nullptr;

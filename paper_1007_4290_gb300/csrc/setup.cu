@@ -37,13 +37,14 @@ constexpr int kBlk = 256;
 template <typename R> struct Tiny;
 template <> struct Tiny<double> {
   static constexpr double dep = 1e-13;    // Gram-Schmidt: dependent-column threshold
-  static constexpr double jac = 1e-15;    // Jacobi: orthogonality tolerance
-  static constexpr double neg = 1e-200;   // Jacobi: negligible column (normalised)
+  static constexpr double jac = 1e-15;    // Jacobi: orthogonality tolerance (about 8 ulp)
+  static constexpr double neg = 1e-28;    // Jacobi: squared norm of a rounding-noise column
+                                          // (normalised: below 1e-14 of the largest column)
 };
 template <> struct Tiny<float> {
   static constexpr float dep = 2e-6f;
-  static constexpr float jac = 1e-7f;
-  static constexpr float neg = 1e-30f;
+  static constexpr float jac = 4e-7f;     // about 7 ulp: tighter only rotates rounding noise
+  static constexpr float neg = 1e-14f;    // below 1e-7 of the largest column: FP32 noise
 };
 
 template <typename R> __device__ __forceinline__ Cx<R> warp_sum(Cx<R> v) {
@@ -488,6 +489,11 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
   for (int e = threadIdx.x; e < rows * w; e += blockDim.x) Rm[(long long)(e / w) * ld + e % w] = Cx<R>(0, 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // lanes per row of the projection update: a power of two, at most 32 and at most
+  // blockDim / s (at least 1); blockDim.x is a multiple of 32
+  int gT = 1;
+  while (gT < 32 && 2 * gT * s <= (int)blockDim.x) gT *= 2;
+  const int rows_per_pass = (int)blockDim.x / gT;
   for (int j = 0; j < w; ++j) {
     const int qc = s_qc;
     R nrm0 = 0;
@@ -508,10 +514,15 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
         }
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < s; i += blockDim.x) {
-        Cx<R> acc = v[i];
-        for (int l = 0; l < qc; ++l) acc -= F[(long long)l * s + i] * c[l];
-        v[i] = acc;
+      // v -= Q c: gT lanes per row share the sum over the kept columns (all threads busy
+      // when the block has fewer rows than threads)
+      for (int i0 = 0; i0 < s; i0 += rows_per_pass) {
+        const int i = i0 + threadIdx.x / gT, sub = threadIdx.x % gT;
+        Cx<R> acc(0, 0);
+        if (i < s)
+          for (int l = sub; l < qc; l += gT) cfma(acc, F[(long long)l * s + i], c[l]);
+        for (int o = gT >> 1; o > 0; o >>= 1) acc += shfl_xor(acc, o);
+        if (i < s && sub == 0) v[i] -= acc;
       }
       __syncthreads();
     }
@@ -533,11 +544,161 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
   if (threadIdx.x == 0) { qcols[u] = s_qc; qmode[u] = 0; }
 }
 
-// Recompression, step 2: for every sibling pair (a, b) with a = list[blockIdx.x],
-// C = R_a R_b^t (qa x qb), one-sided Jacobi C W = P Sigma, truncation, and the small
-// transforms
-//   T_a = (P Sigma)[:, kept] (qa x k'),  T_b = conj(W)[:, kept] (qb x k').
-// qa, qb <= QCAP, the largest core of the plan (setup_alloc).
+// Recompression, step 2a: the cores C = R_a R_b^t (qa x qb, column-major, ld qa, at
+// Cb + (a / 2) QCAP^2) of the sibling pairs a = list[blockIdx.y], one kCT x kCT tile of C
+// per CTA (blockIdx.x).  Two kernels compute them: core_product_cc on CUDA cores (either
+// precision) and, in complex64, core_product_tc on tensor cores; the setup times both on
+// a layer of representative ranks and keeps the faster for each kind of recompression
+// launch (factor_impl).
+constexpr int kCT = 32;    // tile edge in complex entries
+constexpr int kCK = 16;    // complex k chunk staged in shared memory
+
+__device__ __forceinline__ bool core_tile(int qa, int qb, int tile, int& ti, int& tj) {
+  const int ni = (qa + kCT - 1) / kCT, nj = (qb + kCT - 1) / kCT;
+  if (tile >= ni * nj) return false;
+  ti = tile % ni;
+  tj = tile / ni;
+  return true;
+}
+
+// 256 threads: thread (tx, ty) of a 16 x 16 grid owns rows ty, ty + 16 and columns tx,
+// tx + 16 of the tile; the k chunks of R_a and R_b are staged with coalesced loads
+template <typename R>
+__global__ void __launch_bounds__(256) core_product_cc(Geo g, const Cx<R>* __restrict__ Rb,
+                                                       const int* __restrict__ qcols, const int* __restrict__ G_rank,
+                                                       Cx<R>* __restrict__ Cb) {
+  __shared__ Cx<R> As[kCK][kCT + 1], Bs[kCK][kCT + 1];
+  const int a = g.list[blockIdx.y], b = a + 1;
+  const int qa = qcols[a], qb = qcols[b], w = G_rank[a];
+  int ti, tj;
+  if (!core_tile(qa, qb, blockIdx.x, ti, tj)) return;
+  const Cx<R>* Ra = Rb + g.rbo[a];
+  const Cx<R>* Rbb = Rb + g.rbo[b];
+  const int lda = g.cap[a], ldb = g.cap[b];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  Cx<R> acc[2][2];
+  for (int u = 0; u < 2; ++u)
+    for (int v = 0; v < 2; ++v) acc[u][v] = Cx<R>(0, 0);
+  for (int k0 = 0; k0 < w; k0 += kCK) {
+    for (int e = threadIdx.x; e < kCK * kCT; e += blockDim.x) {
+      const int kk = e % kCK, r = e / kCK;
+      const int i = ti * kCT + r, j = tj * kCT + r, k = k0 + kk;
+      As[kk][r] = (i < qa && k < w) ? Ra[(long long)i * lda + k] : Cx<R>(0, 0);
+      Bs[kk][r] = (j < qb && k < w) ? Rbb[(long long)j * ldb + k] : Cx<R>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kCK; ++kk) {
+      const Cx<R> a0 = As[kk][ty], a1 = As[kk][ty + 16], b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  Cx<R>* C = Cb + (long long)(a >> 1) * g.QCAP * g.QCAP;
+  for (int u = 0; u < 2; ++u)
+    for (int v = 0; v < 2; ++v) {
+      const int i = ti * kCT + ty + 16 * u, j = tj * kCT + tx + 16 * v;
+      if (i < qa && j < qb) C[(long long)j * qa + i] = acc[u][v];
+    }
+}
+
+// x = hi + lo with hi the TF32 rounding of x (10 explicit mantissa bits) and lo = x - hi,
+// exact in FP32; a product in three TF32 parts, hi*hi + hi*lo + lo*hi with FP32
+// accumulation, keeps about 2^-21 relative accuracy
+__device__ __forceinline__ void tf32_split(float x, unsigned& hi, unsigned& lo) {
+  hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The complex product as one real product C' = A' B'^t: A' row i = (Re, Im) of row i of
+// R_a interleaved (real k' = 2 l + q), and B' holds for output column n' = 2 j + p
+//   B'[2l][2j] = Re b, B'[2l+1][2j] = -Im b, B'[2l][2j+1] = Im b, B'[2l+1][2j+1] = Re b
+// (b = R_b[j][l]), so that C'[i][2j] = Re C[i][j] and C'[i][2j+1] = Im C[i][j].  Eight
+// warps: warp (wm = warp & 1, wn = warp >> 1) owns tile rows 16 wm .. 16 wm + 15 and the
+// real columns 16 wn .. 16 wn + 15 (two m16n8k8 column tiles).
+__global__ void __launch_bounds__(256) core_product_tc(Geo g, const Cx<float>* __restrict__ Rb,
+                                                       const int* __restrict__ qcols, const int* __restrict__ G_rank,
+                                                       Cx<float>* __restrict__ Cb) {
+  __shared__ Cx<float> As[kCT][kCK + 1], Bs[kCT][kCK + 1];
+  const int a = g.list[blockIdx.y], b = a + 1;
+  const int qa = qcols[a], qb = qcols[b], w = G_rank[a];
+  int ti, tj;
+  if (!core_tile(qa, qb, blockIdx.x, ti, tj)) return;
+  const Cx<float>* Ra = Rb + g.rbo[a];
+  const Cx<float>* Rbb = Rb + g.rbo[b];
+  const int lda = g.cap[a], ldb = g.cap[b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wm = warp & 1, wn = warp >> 1;
+  const int gid = lane >> 2, tig = lane & 3;
+  float c[2][4] = {}, c2[2][4] = {};
+  for (int k0 = 0; k0 < w; k0 += kCK) {
+    for (int e = threadIdx.x; e < kCK * kCT; e += blockDim.x) {
+      const int kk = e % kCK, r = e / kCK;
+      const int i = ti * kCT + r, j = tj * kCT + r, k = k0 + kk;
+      As[r][kk] = (i < qa && k < w) ? Ra[(long long)i * lda + k] : Cx<float>(0.f, 0.f);
+      Bs[r][kk] = (j < qb && k < w) ? Rbb[(long long)j * ldb + k] : Cx<float>(0.f, 0.f);
+    }
+    __syncthreads();
+    // real k' in steps of 8 over the chunk's 2 kCK real columns
+#pragma unroll
+    for (int ks = 0; ks < 2 * kCK; ks += 8) {
+      // A fragment: rows 16 wm + gid (+ 8), real columns ks + tig (+ 4)
+      unsigned ah[4], al[4];
+      {
+        const int r0 = 16 * wm + gid, r1 = r0 + 8;
+        const int k1 = ks + tig, k2 = ks + tig + 4;
+        const float v0 = (k1 & 1) ? As[r0][k1 >> 1].im : As[r0][k1 >> 1].re;
+        const float v1 = (k1 & 1) ? As[r1][k1 >> 1].im : As[r1][k1 >> 1].re;
+        const float v2 = (k2 & 1) ? As[r0][k2 >> 1].im : As[r0][k2 >> 1].re;
+        const float v3 = (k2 & 1) ? As[r1][k2 >> 1].im : As[r1][k2 >> 1].re;
+        tf32_split(v0, ah[0], al[0]);
+        tf32_split(v1, ah[1], al[1]);
+        tf32_split(v2, ah[2], al[2]);
+        tf32_split(v3, ah[3], al[3]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        // B fragment: real rows ks + tig (+ 4), real output column 16 wn + 8 nt + gid
+        const int np = 16 * wn + 8 * nt + gid;
+        const int j = np >> 1, p = np & 1;
+        float bv[2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int kp = ks + tig + 4 * h2;
+          const Cx<float> bb = Bs[j][kp >> 1];
+          const int q = kp & 1;
+          bv[h2] = p == 0 ? (q == 0 ? bb.re : -bb.im) : (q == 0 ? bb.im : bb.re);
+        }
+        unsigned bh0, bl0, bh1, bl1;
+        tf32_split(bv[0], bh0, bl0);
+        tf32_split(bv[1], bh1, bl1);
+        mma_m16n8k8_tf32(c[nt], ah, bh0, bh1);
+        mma_m16n8k8_tf32(c2[nt], al, bh0, bh1);
+        mma_m16n8k8_tf32(c2[nt], ah, bl0, bl1);
+      }
+    }
+    __syncthreads();
+  }
+  Cx<float>* C = Cb + (long long)(a >> 1) * g.QCAP * g.QCAP;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    const int j = tj * kCT + ((16 * wn + 8 * nt) >> 1) + tig;   // output columns 2 tig, 2 tig + 1 of the n-tile
+    const int i0 = ti * kCT + 16 * wm + gid, i1 = i0 + 8;
+    if (j < qb) {
+      if (i0 < qa) C[(long long)j * qa + i0] = Cx<float>(c[nt][0] + c2[nt][0], c[nt][1] + c2[nt][1]);
+      if (i1 < qa) C[(long long)j * qa + i1] = Cx<float>(c[nt][2] + c2[nt][2], c[nt][3] + c2[nt][3]);
+    }
+  }
+}
+
 // Shuffle-sum within aligned groups of GW lanes (GW = 16 or 32).
 template <typename R> __device__ __forceinline__ R group_sum_r(R v, int GW) {
   for (int o = GW >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -548,10 +709,14 @@ template <typename R> __device__ __forceinline__ Cx<R> group_sum(Cx<R> v, int GW
   return v;
 }
 
+// Recompression, step 2b: for every sibling pair (a, b) with a = list[blockIdx.x], the
+// core C (step 2a), one-sided Jacobi C W = P Sigma, truncation, and the small transforms
+//   T_a = (P Sigma)[:, kept] (qa x k'),  T_b = conj(W)[:, kept] (qb x k').
+// qa, qb <= QCAP, the largest core of the plan (setup_alloc).
 template <typename R>
-__global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Rb, const int* __restrict__ qcols,
+__global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Cb, const int* __restrict__ qcols,
                            const int* __restrict__ G_rank, Cx<R>* __restrict__ Wb, Cx<R>* __restrict__ Tx,
-                           int* __restrict__ newrank, int smem_entries) {
+                           int* __restrict__ newrank, int smem_entries, R frz) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int a = g.list[blockIdx.x], b = a + 1, t = a >> 1;
   const int qa = qcols[a], qb = qcols[b], w = G_rank[a];
@@ -565,18 +730,13 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Rb, cons
   int* order = reinterpret_cast<int*>(sig + g.QCAP + 1);                          // [QCAP]
   __shared__ int s_rot, s_keep;
   __shared__ R s_scale;
-  const Cx<R>* Ra = Rb + g.rbo[a];
-  const Cx<R>* Rbm = Rb + g.rbo[b];
-  const int lda = g.cap[a], ldb = g.cap[b];
   if (qa == 0 || qb == 0) {
     if (threadIdx.x == 0) { newrank[a] = 0; newrank[b] = 0; }
     return;
   }
-  for (int e = threadIdx.x; e < qa * qb; e += blockDim.x) {
-    const int i = e % qa, j = e / qa;
-    Cx<R> acc(0, 0);
-    for (int l = 0; l < w; ++l) cfma(acc, Ra[(long long)i * lda + l], Rbm[(long long)j * ldb + l]);
-    C[e] = acc;
+  {
+    const Cx<R>* Cg = Cb + (long long)t * g.QCAP * g.QCAP;     // the core from step 2a
+    for (int e = threadIdx.x; e < qa * qb; e += blockDim.x) C[e] = Cg[e];
   }
   for (int e = threadIdx.x; e < qb * qb; e += blockDim.x) {
     const int i = e % qb, j = e / qb;
@@ -633,7 +793,10 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Rb, cons
           }
         al = group_sum_r(al, GW); be = group_sum_r(be, GW); ga = group_sum(ga, GW);
         const R ag = sqrt(abs2(ga));
-        const bool rot = live && al >= Tiny<R>::neg && be >= Tiny<R>::neg && ag > Tiny<R>::jac * sqrt(al) * sqrt(be);
+        // a column whose squared norm is below frz (relative to the largest, 1 after the
+        // normalisation) stays below it under every rotation and is truncated in the end:
+        // it is left alone, so the sweeps stop once the significant columns are orthogonal
+        const bool rot = live && al >= frz && be >= frz && ag > Tiny<R>::jac * sqrt(al) * sqrt(be);
         if (rot) {
           if (gl == 0) s_rot = 1;
           const Cx<R> e(ga.re / ag, ga.im / ag);
@@ -699,32 +862,69 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Rb, cons
   }
 }
 
-// Recompression, step 3, for the nodes u = list[blockIdx.x]: F'_u = Q_u T_u (T_u itself
-// on the dense path), computed into the node's region of the scratch buffer Fs and copied
-// back into G_F.
+// Recompression, step 3, for the nodes u = list[blockIdx.y]: F'_u = Q_u T_u (sz(u) x kr,
+// column-major; T_u itself on the dense path) into the node's region of the scratch
+// buffer Fs, one kCT x kCT tile per CTA (blockIdx.x), the k chunks of Q_u and T_u staged
+// with coalesced loads; recompress_copy then moves it into G_F (Q_u is read from G_F
+// until every tile is done).
 template <typename R>
-__global__ void recompress_apply(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ qcols,
-                                 const int* __restrict__ qmode, const Cx<R>* __restrict__ Tx,
-                                 const int* __restrict__ newrank, Cx<R>* __restrict__ Fs, int* __restrict__ G_rank) {
-  const int u = g.list[blockIdx.x];
+__global__ void __launch_bounds__(256) recompress_gemm(Geo g, const Cx<R>* __restrict__ G_F,
+                                                       const int* __restrict__ qcols, const int* __restrict__ qmode,
+                                                       const Cx<R>* __restrict__ Tx, const int* __restrict__ newrank,
+                                                       Cx<R>* __restrict__ Fs) {
+  __shared__ Cx<R> Qs[kCK][kCT + 1], Ts[kCK][kCT + 1];
+  const int u = g.list[blockIdx.y];
   const int s = g.sz[u], qc = qcols[u], kr = newrank[u];
+  const int ni = (s + kCT - 1) / kCT, nj = (kr + kCT - 1) / kCT;
+  if ((int)blockIdx.x >= ni * nj) return;
+  const int ti = blockIdx.x % ni, tj = blockIdx.x / ni;
   const Cx<R>* Qu = G_F + g.gfo[u];
   const Cx<R>* T = Tx + (long long)u * g.QCAP * g.r_max;
   Cx<R>* S = Fs + g.gfo[u];
   if (qmode[u]) {
-    for (int e = threadIdx.x; e < s * kr; e += blockDim.x) {
-      const int i = e % s, j = e / s;
-      S[(long long)j * s + i] = T[(long long)j * g.QCAP + i];
+    for (int e = threadIdx.x; e < kCT * kCT; e += blockDim.x) {
+      const int i = ti * kCT + e % kCT, j = tj * kCT + e / kCT;
+      if (i < s && j < kr) S[(long long)j * s + i] = T[(long long)j * g.QCAP + i];
     }
-  } else {
-    for (int e = threadIdx.x; e < s * kr; e += blockDim.x) {
-      const int i = e % s, j = e / s;
-      Cx<R> acc(0, 0);
-      for (int l = 0; l < qc; ++l) cfma(acc, Qu[(long long)l * s + i], T[(long long)j * g.QCAP + l]);
-      S[(long long)j * s + i] = acc;
-    }
+    return;
   }
-  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  Cx<R> acc[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) acc[a][b] = Cx<R>(0, 0);
+  for (int k0 = 0; k0 < qc; k0 += kCK) {
+    for (int e = threadIdx.x; e < kCK * kCT; e += blockDim.x) {
+      const int r = e % kCT, kq = e / kCT;          // Q: consecutive threads, consecutive rows
+      const int i = ti * kCT + r, k = k0 + kq;
+      Qs[kq][r] = (i < s && k < qc) ? Qu[(long long)k * s + i] : Cx<R>(0, 0);
+      const int kt = e % kCK, cc = e / kCK;         // T: consecutive threads, consecutive k
+      const int j = tj * kCT + cc, k2 = k0 + kt;
+      Ts[kt][cc] = (j < kr && k2 < qc) ? T[(long long)j * g.QCAP + k2] : Cx<R>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kCK; ++kk) {
+      const Cx<R> a0 = Qs[kk][ty], a1 = Qs[kk][ty + 16], b0 = Ts[kk][tx], b1 = Ts[kk][tx + 16];
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = ti * kCT + ty + 16 * a, j = tj * kCT + tx + 16 * b;
+      if (i < s && j < kr) S[(long long)j * s + i] = acc[a][b];
+    }
+}
+
+template <typename R>
+__global__ void recompress_copy(Geo g, const Cx<R>* __restrict__ Fs, const int* __restrict__ newrank,
+                                Cx<R>* __restrict__ G_F, int* __restrict__ G_rank) {
+  const int u = g.list[blockIdx.x];
+  const int s = g.sz[u], kr = newrank[u];
+  const Cx<R>* S = Fs + g.gfo[u];
   Cx<R>* F = G_F + g.gfo[u];
   for (int e = threadIdx.x; e < s * kr; e += blockDim.x) F[e] = S[e];
   if (threadIdx.x == 0) G_rank[u] = kr;
@@ -779,7 +979,7 @@ struct SetupWork {
   int* d_lists = nullptr;
   void *S_leaf = nullptr, *S_F = nullptr, *G_leaf = nullptr, *G_F = nullptr, *G_F2 = nullptr;
   void *Y = nullptr, *W = nullptr, *Qr = nullptr, *PQ = nullptr, *M = nullptr, *Rb = nullptr;
-  void *Wb = nullptr, *Tx = nullptr;
+  void *Wb = nullptr, *Tx = nullptr, *Cb = nullptr;
   int *S_rank = nullptr, *G_rank = nullptr, *qcols = nullptr, *qmode = nullptr, *newrank = nullptr;
 };
 
@@ -787,7 +987,7 @@ void hsw_setup_free(hsweep_s* h) {
   if (!h->sw) return;
   SetupWork* w = h->sw;
   void* ptrs[] = {w->d_sfo, w->d_gfo, w->d_qro, w->d_rbo, w->d_rowleaf, w->d_cap, w->d_lists, w->S_leaf, w->S_F,
-                  w->G_leaf, w->G_F, w->G_F2, w->Y, w->W, w->Qr, w->PQ, w->M, w->Rb, w->Wb, w->Tx, w->S_rank,
+                  w->G_leaf, w->G_F, w->G_F2, w->Y, w->W, w->Qr, w->PQ, w->M, w->Rb, w->Wb, w->Tx, w->Cb, w->S_rank,
                   w->G_rank, w->qcols, w->qmode, w->newrank};
   for (void* p : ptrs) hsw_release(h, p);
   delete w;
@@ -889,6 +1089,7 @@ static int setup_alloc(hsweep_s* h) {
   A(w->Rb, std::max(ro, 1LL) * es);
   A(w->Wb, (long long)nn * w->QCAP * w->QCAP * es);
   A(w->Tx, (long long)nn * w->QCAP * h->r_max * es);
+  A(w->Cb, (long long)(nn / 2) * w->QCAP * w->QCAP * es);
   A(w->S_rank, nn * sizeof(int));
   A(w->G_rank, nn * sizeof(int));
   A(w->qcols, nn * sizeof(int));
@@ -949,8 +1150,8 @@ static int factor_impl(hsweep_s* h) {
     const void* ks[] = {(const void*)schur_leaves<R>, (const void*)schur_factors<R>, (const void*)leaf_inverse<R>,
                         (const void*)tsmm_reduce<R>, (const void*)tsmm_expand<R>, (const void*)core_dots<R>,
                         (const void*)core_inverse<R>, (const void*)woodbury_form<R>, (const void*)woodbury_append<R>,
-                        (const void*)qr_cgs2<R>, (const void*)svd_jacobi<R>, (const void*)recompress_apply<R>,
-                        (const void*)store_layer<R>};
+                        (const void*)qr_cgs2<R>, (const void*)svd_jacobi<R>, (const void*)recompress_gemm<R>,
+                        (const void*)recompress_copy<R>, (const void*)store_layer<R>, (const void*)core_product_cc<R>};
     for (const void* k : ks)
       HSW_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
   }
@@ -960,22 +1161,79 @@ static int factor_impl(hsweep_s* h) {
   if (core_smem > 227 * 1024 || qr_smem > 227 * 1024 || svd_smem > 227 * 1024 || svd_entries < QCAP * QCAP)
     return HSWEEP_ERR_ARG;
 
-  // QR (or the dense path), SVD of the cores and the new factors, for nn_list nodes whose
-  // list starts at node_off and their np_list left siblings at pair_off
-  auto recompress = [&](int node_off, int nn_list, int pair_off, int np_list) {
-    if (nn_list <= 0) return;
+  // Autotuning of the core products (step 2a), complex64 only: on layer tune_m, the first
+  // launch of each kind (0: the recompressions after a depth step, 1: the once-per-layer
+  // recompression) runs both kernels, timed with CUDA events, and the faster one serves that
+  // kind of launch from then on; before it, and in complex128, the CUDA-core kernel runs.
+  const int tune_m = h->n / 2;
+  // Jacobi: columns below a tenth of the truncation threshold (squared, relative) are frozen
+  const R frz = (R)std::max((double)Tiny<R>::neg, 0.01 * h->eps_H * h->eps_H);
+  const int core_tiles = ((QCAP + kCT - 1) / kCT) * ((QCAP + kCT - 1) / kCT);
+  const int gemm_tiles = ((h->tree.maxsz(1) + kCT - 1) / kCT) * ((h->r_max + kCT - 1) / kCT);
+  Cx<R>* Cb = (Cx<R>*)w->Cb;
+  int m_cur = 0;
+  auto core_product = [&](const Geo& gp, int np_list, int kind) -> int {
+    const dim3 grid(core_tiles, np_list);
+    const bool f32 = sizeof(R) == 4;
+    auto run = [&](int mode) {
+      if constexpr (sizeof(R) == 4) {
+        if (mode == 1) {
+          core_product_tc<<<grid, 256, 0, st>>>(gp, (const Cx<float>*)Rb, w->qcols, w->G_rank, (Cx<float>*)Cb);
+          return;
+        }
+      }
+      core_product_cc<R><<<grid, 256, 0, st>>>(gp, Rb, w->qcols, w->G_rank, Cb);
+    };
+    if (h->opt.core_kernel > 0) {          // fixed by the caller
+      run(f32 && h->opt.core_kernel == 2 ? 1 : 0);
+      h->nlaunch += 1;
+      return HSWEEP_OK;
+    }
+    if (f32 && h->core_mode[kind] < 0 && m_cur == tune_m) {
+      cudaEvent_t ev[3];
+      for (auto& e : ev) HSW_CUDA(cudaEventCreate(&e));
+      HSW_CUDA(cudaEventRecord(ev[0], st));
+      run(0);
+      HSW_CUDA(cudaEventRecord(ev[1], st));
+      run(1);
+      HSW_CUDA(cudaEventRecord(ev[2], st));
+      HSW_CUDA(cudaEventSynchronize(ev[2]));
+      float t0 = 0, t1 = 0;
+      HSW_CUDA(cudaEventElapsedTime(&t0, ev[0], ev[1]));
+      HSW_CUDA(cudaEventElapsedTime(&t1, ev[1], ev[2]));
+      for (auto& e : ev) cudaEventDestroy(e);
+      h->core_ms[kind][0] = t0;
+      h->core_ms[kind][1] = t1;
+      h->core_mode[kind] = t1 < t0 ? 1 : 0;
+      h->nlaunch += 2;
+      return HSWEEP_OK;
+    }
+    run(f32 && h->core_mode[kind] == 1 ? 1 : 0);
+    h->nlaunch += 1;
+    return HSWEEP_OK;
+  };
+
+  // QR (or the dense path), the cores, their SVD and the new factors, for nn_list nodes
+  // whose list starts at node_off and their np_list left siblings at pair_off
+  auto recompress = [&](int node_off, int nn_list, int pair_off, int np_list, int kind) -> int {
+    if (nn_list <= 0) return HSWEEP_OK;
     Geo gl = g;
     gl.list = w->d_lists + node_off;
     qr_cgs2<R><<<nn_list, 1024, qr_smem, st>>>(gl, G_F, w->G_rank, Rb, w->qcols, w->qmode);
     Geo gp = g;
     gp.list = w->d_lists + pair_off;
-    svd_jacobi<R><<<np_list, 1024, svd_smem, st>>>(gp, h->eps_H, Rb, w->qcols, w->G_rank, Wb, Tx, w->newrank,
-                                                   svd_entries);
-    recompress_apply<R><<<nn_list, kBlk, 0, st>>>(gl, G_F, w->qcols, w->qmode, Tx, w->newrank, G_F2, w->G_rank);
-    h->nlaunch += 3;
+    int rc = core_product(gp, np_list, kind);
+    if (rc) return rc;
+    svd_jacobi<R><<<np_list, 1024, svd_smem, st>>>(gp, h->eps_H, Cb, w->qcols, w->G_rank, Wb, Tx, w->newrank,
+                                                   svd_entries, frz);
+    recompress_gemm<R><<<dim3(gemm_tiles, nn_list), 256, 0, st>>>(gl, G_F, w->qcols, w->qmode, Tx, w->newrank, G_F2);
+    recompress_copy<R><<<nn_list, kBlk, 0, st>>>(gl, G_F2, w->newrank, G_F, w->G_rank);
+    h->nlaunch += 4;
+    return HSWEEP_OK;
   };
 
   for (int m = 0; m < h->n; ++m) {
+    m_cur = m;
     const Cx<R>* Tprev = m > 0 ? fac + (long long)(m - 1) * h->layer_stride : nullptr;
     const int* rprev = m > 0 ? h->d_rank + (long long)(m - 1) * nn : nullptr;
     schur_leaves<R><<<h->nleaves, 64, 0, st>>>(g, m, h->d_diag_m, h->d_east_m, h->d_north_m, Tprev, S_leaf);
@@ -1008,11 +1266,15 @@ static int factor_impl(hsweep_s* h) {
       woodbury_append<R><<<n_below1, kBlk, 0, st>>>(g, d, w->S_rank, Y, Wv, G_F, w->G_rank, G_leaf);
       h->nlaunch += 1;
       // the blocks of the non-deferred depths that this depth step changed
-      recompress(w->big_nodes_off[d], w->big_nodes_off[d + 1] - w->big_nodes_off[d], w->big_pairs_off[d],
-                 w->big_pairs_off[d + 1] - w->big_pairs_off[d]);
+      int rc = recompress(w->big_nodes_off[d], w->big_nodes_off[d + 1] - w->big_nodes_off[d], w->big_pairs_off[d],
+                          w->big_pairs_off[d + 1] - w->big_pairs_off[d], 0);
+      if (rc) return rc;
     }
     // the blocks of the deferred depths, once per layer, in their final form
-    recompress(w->small_nodes_off, w->small_nodes, w->small_pairs_off, w->small_pairs);
+    {
+      int rc = recompress(w->small_nodes_off, w->small_nodes, w->small_pairs_off, w->small_pairs, 1);
+      if (rc) return rc;
+    }
     if (h->strong_R > 0) {
       // strongly admissible T~_m (strong.cu), then one recompression of every sibling pair:
       // the expanded layout can carry more columns than a block has rows (small blocks,
@@ -1021,7 +1283,8 @@ static int factor_impl(hsweep_s* h) {
       int rc = hsw_strong_project(h, m, G_F, w->G_rank, G_F2, w->d_gfo, w->gfo_total);
       if (rc) return rc;
       std::swap(G_F, G_F2);
-      recompress(w->all_nodes_off, w->all_nodes, w->all_pairs_off, w->all_pairs);
+      rc = recompress(w->all_nodes_off, w->all_nodes, w->all_pairs_off, w->all_pairs, 1);
+      if (rc) return rc;
     }
     store_layer<R><<<nn, kBlk, 0, st>>>(g, G_leaf, G_F, w->G_rank, fac + (long long)m * h->layer_stride,
                                         h->d_off, h->d_rank + (long long)m * nn);

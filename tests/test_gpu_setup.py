@@ -39,14 +39,17 @@ def _dense_layers(h, n, leaf, r_max, ms):
     return out
 
 
-@pytest.mark.parametrize("n,prec,tol", [(31, 0, 1e-10), (37, 0, 1e-10), (64, 0, 1e-9), (31, 1, 2e-4)])
-def test_setup_without_truncation_is_the_exact_sweep(hs, n, prec, tol):
+@pytest.mark.parametrize("n,prec,tol,core", [(31, 0, 1e-10, 0), (37, 0, 1e-10, 0), (64, 0, 1e-9, 0), (31, 1, 2e-4, 0),
+                                          (31, 1, 2e-4, 1), (64, 1, 2e-4, 2), (37, 1, 2e-4, 2)])
+def test_setup_without_truncation_is_the_exact_sweep(hs, n, prec, tol, core):
+    # core: the recompression cores on the autotuned kernel (0), on CUDA cores (1) or on
+    # tensor cores with TF32 operands in three parts (2)
     c, omega, pml = _problem(n, 1)
     disc = Discretization(c, omega, pml)
     T = setup_exact(disc)
     r_max = min(56, (n + 1) // 2)
     h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 0.0,
-                        hs.default_opts(precision=prec, r_max=r_max))
+                        hs.default_opts(precision=prec, r_max=r_max, core_kernel=core))
     assert h.status()[0] == 0
     ms = [0, 1, n // 3, n // 2, n - 1]
     D = _dense_layers(h, n, 8, r_max, ms)
@@ -91,4 +94,20 @@ def test_apply_with_gpu_factors_matches_exact_sweep_on_them(hs, n, prec, nrhs):
         ref = solve_exact(disc, T, R[s])
         err = np.linalg.norm(Z[s] - ref) / np.linalg.norm(ref)
         assert err < (1e-11 if prec == 0 else 1e-4), (s, err)
+    h.free()
+
+
+def test_core_product_autotuning_reports_its_choice(hs):
+    # complex64: the setup times the CUDA-core and tensor-core kernels of the recompression
+    # cores on its middle layer and keeps the faster; complex128 always uses CUDA cores
+    w = synth.workload("n511_lens")
+    c = torch.tensor(w["c"], device="cuda")
+    h = hs.hsweep_setup(c, w["omega"], w["pml"], w["eps_H"], hs.default_opts(precision=hs.MIXED))
+    t = h.setup_tuning()
+    h.free()
+    assert t["per_layer"] in (0, 1), t
+    assert all(x > 0 for x in t["ms"][1]), t
+    assert t["per_layer"] == (1 if t["ms"][1][1] < t["ms"][1][0] else 0)
+    h = hs.hsweep_setup(c[:64, :64].contiguous(), 2 * np.pi * 4, 8, 1e-6, hs.default_opts(precision=hs.FP64))
+    assert h.setup_tuning()["per_layer"] == -1
     h.free()
