@@ -72,9 +72,9 @@ def sweep_work(h, n, nrhs, elem_bytes):
 # keyed by workload and right-hand sides, with the SHA-256 of the kernel source they were
 # taken on: a changed kernel reports null instead of a stale number.
 SWEEP_TRAFFIC = {
-    # profiles/sweep_team_n1023_random_64rhs_dram.md: 3.97 GB read + 1.57 GB written
-    "n1023_random/64": {"sha256": "75467c6fcf28dfa9fd94fa0d13c92a263363a102bddc6ec57678f988fd9e60fa",
-                        "bytes": 5.54e9},
+    # profiles/sweep_team_n1023_random_64rhs_dram.md: 3.98 GB read + 1.57 GB written
+    "n1023_random/64": {"sha256": "b04e7c62c70f32ff0871025f7e90165c0ff2cd4d87d87c17caa185b508ee5fef",
+                        "bytes": 5.553e9},
 }
 TEAM_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_team.cu")
 
@@ -216,8 +216,8 @@ def oracle_apply_steps(disc, T, f):
 
 def cpu_baseline_run(out_json, uref_npy, stop_file, hard_s):
     """The CPU leg of the bench, run in its own process while the GPU legs run (started
-    before any GPU call).  (1) O4: the oracle's setup chain from layer 0 until the GPU legs
-    are done (stop_file appears) or hard_s seconds, every layer timed; then its sweeps over
+    before any GPU call).  (1) O4: the oracle's setup chain from layer 0 over the whole
+    domain, or until hard_s seconds (or stop_file appears), every layer timed; then its sweeps over
     all built layers, and, when the chain is complete, one whole preconditioned GMRES solve
     of source 0 (oracle.gmres, tolerance SOLVE_TOL).  (2) O2: the sparse direct solve of
     source 0 (factor and solve timed), whose solution is saved for the error of the GPU
@@ -267,12 +267,11 @@ def start_cpu_baseline(tmpdir, hard_s=600.0):
 
 
 def finish_cpu_baseline(proc, paths, threads, applies_per_solve, timeout_s=900.0):
-    """Stop the chain, wait for the CPU process, and compose the baseline: measured when
-    the chain was complete (one whole solve), else the built layers' measured setup time
-    plus the last tenth's mean per-layer time for the rest, and the measured per-step
-    apply time x (2n - 1) steps x applies_per_solve."""
+    """Wait for the CPU process (its chain stops by itself at its time limit) and compose
+    the baseline: measured when the chain was complete (one whole solve), else the built
+    layers' measured setup time plus the last tenth's mean per-layer time for the rest, and
+    the measured per-step apply time x (2n - 1) steps x applies_per_solve."""
     import numpy as np
-    open(paths["stop"], "w").close()
     try:
         _, err = proc.communicate(timeout=timeout_s)
     except subprocess.TimeoutExpired:
@@ -445,6 +444,15 @@ def main():
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     info = h.info()
+    setup_tuning = h.setup_tuning()
+    # ranks of the factorised blocks per depth (min / mean / max over every 16th layer)
+    Ld, _ = _tree_sizes(n)
+    per_depth = {d: [] for d in range(1, Ld + 1)}
+    for m in range(0, n, 16):
+        rk = h.layer_ranks(m)
+        for v in range(2, 1 << (Ld + 1)):
+            per_depth[v.bit_length() - 1].append(rk[v])
+    ranks = {str(d): [int(min(r)), round(float(np.mean(r)), 1), int(max(r))] for d, r in per_depth.items() if r}
 
     def step(u):
         u.zero_()
@@ -648,6 +656,8 @@ def main():
                        "l2": "inputs larger than L2 (1 GB RHS batch, factors %.2f GB)" % (
                            stored * info["bytes_per_entry"] / 1e9)},
             "setup_s": setup_s,
+            "setup_tuning": setup_tuning,
+            "ranks_per_depth": ranks,
             "gmres_iters": {"min": min(it), "max": max(it), "mean": float(np.mean(it))},
             "relres_max": max(rr),
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(f_h.numel() * 16),
@@ -837,9 +847,10 @@ def run_parts(args):
 
 
 # applies of M per solve of the GPU arm's mixed solve at this workload (bench.py's
-# sweep_launches_per_step: M f, the inner GMRES steps around one FP64 refinement, and the
-# residual checks); the reference arm's per-solve time uses the same count
-REFERENCE_APPLIES_PER_SOLVE = 6
+# sweep_launches_per_step: M f, two inner GMRES steps, the residual check of the one FP64
+# refinement step and its inner GMRES step); the reference arm's per-solve time uses the
+# same count
+REFERENCE_APPLIES_PER_SOLVE = 5
 
 
 def run_reference(args, world, rank):

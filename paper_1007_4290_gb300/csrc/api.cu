@@ -234,6 +234,7 @@ extern "C" int hsweep_create(const double* c_dev, double omega, int n, int pml_w
 extern "C" int hsweep_setup(const double* c_dev, double omega, int n, int pml_width, double eps_H,
                             const hsweep_opts* opt, void* stream, hsweep_t* out) {
   if (!out) return HSWEEP_ERR_ARG;
+  NvtxRange range("hsweep_setup");
   hsweep_t h = nullptr;
   int rc = create_impl(c_dev, omega, n, pml_width, eps_H, opt, stream, &h);
   if (rc != HSWEEP_OK) return rc;
@@ -258,6 +259,7 @@ extern "C" int hsweep_setup(const double* c_dev, double omega, int n, int pml_wi
 
 extern "C" int hsweep_apply(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!r || !z))) return HSWEEP_ERR_ARG;
+  NvtxRange range("hsweep_apply");
   const char* rb = (const char*)r;
   const char* zb = (const char*)z;
   size_t bytes = (size_t)nrhs * h->N * sizeof(hsw_c128);
@@ -293,6 +295,7 @@ extern "C" int hsweep_solve(hsweep_t h, const hsw_c128* f, hsw_c128* u, int nrhs
                             int* iters_out, double* relres_out) {
   if (!h || nrhs < 0 || (nrhs > 0 && (!f || !u)) || !(tol > 0) || tol >= 1) return HSWEEP_ERR_ARG;
   if (nrhs == 0) return HSWEEP_OK;
+  NvtxRange range("hsweep_solve");
   if (h->dir > 0)
     return hsw_solve(h, reinterpret_cast<const c128*>(f), reinterpret_cast<c128*>(u), nrhs, tol,
                      iters_out, relres_out);
@@ -314,6 +317,7 @@ extern "C" int hsweep_grad(hsweep_t h, const hsw_c128* f, int nsrc, const int* r
                            const hsw_c128* d, double* grad, double* misfit_out, double tol) {
   if (!h || nsrc < 1 || nrec < 1 || !f || !rec_idx || !d || !grad || !(tol > 0) || tol >= 1)
     return HSWEEP_ERR_ARG;
+  NvtxRange range("hsweep_grad");
   if (h->dir > 0)
     return hsw_grad(h, reinterpret_cast<const c128*>(f), nsrc, rec_idx, nrec,
                     reinterpret_cast<const c128*>(d), grad, misfit_out, tol);

@@ -10,7 +10,7 @@
 template <typename R>
 struct alignas(2 * sizeof(R)) Cx {
   R re, im;
-  __host__ __device__ Cx() {}
+  Cx() = default;
   __host__ __device__ constexpr Cx(R a, R b = R(0)) : re(a), im(b) {}
 };
 

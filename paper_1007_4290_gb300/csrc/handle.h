@@ -3,7 +3,17 @@
 #include <array>
 #include <utility>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 #include "common.cuh"
+
+// NVTX range over a phase of the method (setup, a setup layer, apply, solve, a GMRES step,
+// gradient), visible on profiler timelines; a push and a pop cost nanoseconds without a tool
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Cluster tree of one layer (Section 2.3): heap-indexed nodes, root = 1, children of v
 // are 2v and 2v+1; a node [lo, lo+sz) of size s splits into ceil(s/2) and floor(s/2)

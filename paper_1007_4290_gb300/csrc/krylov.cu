@@ -357,6 +357,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     bool any = false;
     for (int s = 0; s < nrhs; ++s) any |= run[s] != 0;
     if (!any) break;
+    NvtxRange range("gmres step");
     c128 *vj, *vn;
     if ((rc = basis(h, j, &vj))) return rc;
     if ((rc = basis(h, j + 1, &vn))) return rc;

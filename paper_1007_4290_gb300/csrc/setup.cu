@@ -333,16 +333,24 @@ __global__ void core_inverse(Geo g, int d, int m, const int* __restrict__ S_rank
   const R tiny = (sizeof(R) == 8 ? R(1e-30) : R(1e-14)) * mx;   // on |pivot|^2
   bool bad = false;
   for (int kk = 0; kk < n2; ++kk) {
-    if (threadIdx.x == 0) {
-      int p = kk;
-      R best = abs2(A[kk * n2 + kk]);
-      for (int a = kk + 1; a < n2; ++a) {
-        R v = abs2(A[a * n2 + kk]);
+    if (threadIdx.x < 32) {
+      // partial pivoting: warp 0 finds the largest |A[a][kk]|, a >= kk (ties: the smallest a)
+      int p = n2;
+      R best = R(-1);
+      for (int a = kk + (int)threadIdx.x; a < n2; a += 32) {
+        const R v = abs2(A[a * n2 + kk]);
         if (v > best) { best = v; p = a; }
       }
-      s_p = p;
-      s_best = best;
-      piv[kk] = p;
+      for (int o = 16; o > 0; o >>= 1) {
+        const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (threadIdx.x == 0) {
+        s_p = p;
+        s_best = best;
+        piv[kk] = p;
+      }
     }
     __syncthreads();
     if (!(s_best > tiny)) { bad = true; break; }
@@ -463,10 +471,13 @@ __global__ void woodbury_append(Geo g, int d, const int* __restrict__ S_rank, co
 // a factor with at least as many columns as rows (w >= sz(u)) takes the dense path,
 // Q = I and R = F_u (qcols = sz(u), qmode = 1); otherwise Gram-Schmidt QR (twice
 // orthogonalised) of F_u in place, the Q columns compacted to the independent ones and
-// R (qc x w) written out (qmode = 0).  R is row-major with leading dimension cap(u).
+// R (qc x w) written out (qmode = 0).  R is row-major with leading dimension cap(u).  When
+// F_u fits the kernel's shared memory (qs_entries), the orthogonalisation runs there and
+// the kept columns are written back at the end (every projection reads all earlier
+// columns: O(w^2 s) reads that would otherwise go to L2).
 template <typename R>
 __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ G_rank, Cx<R>* __restrict__ Rb,
-                        int* __restrict__ qcols, int* __restrict__ qmode) {
+                        int* __restrict__ qcols, int* __restrict__ qmode, int qs_entries) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int u = g.list[blockIdx.x];
   const int s = g.sz[u], w = G_rank[u], ld = g.cap[u];
@@ -483,10 +494,15 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
   Cx<R>* v = reinterpret_cast<Cx<R>*>(sm);                // [s]
   Cx<R>* c = v + s;                                        // [QCAP]
   R* red = reinterpret_cast<R*>(c + g.QCAP);               // [32]
+  const size_t qs_off = ((size_t)(s + g.QCAP) * sizeof(Cx<R>) + 32 * sizeof(R) + 15) & ~size_t(15);
+  const bool qsh = (long long)s * w <= qs_entries;
+  Cx<R>* Fq = qsh ? reinterpret_cast<Cx<R>*>(sm + qs_off) : F;   // the columns being orthogonalised
   __shared__ int s_qc;
   if (threadIdx.x == 0) s_qc = 0;
   const int rows = min(s, ld);
   for (int e = threadIdx.x; e < rows * w; e += blockDim.x) Rm[(long long)(e / w) * ld + e % w] = Cx<R>(0, 0);
+  if (qsh)
+    for (int e = threadIdx.x; e < s * w; e += blockDim.x) Fq[e] = F[e];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   // lanes per row of the projection update: a power of two, at most 32 and at most
@@ -498,7 +514,7 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
     const int qc = s_qc;
     R nrm0 = 0;
     for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      v[i] = F[(long long)j * s + i];
+      v[i] = Fq[(long long)j * s + i];
       nrm0 += abs2(v[i]);
     }
     nrm0 = block_sum(nrm0, red);
@@ -506,7 +522,7 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
     for (int pass = 0; pass < 2; ++pass) {
       for (int l = warp; l < qc; l += nw) {
         Cx<R> acc(0, 0);
-        for (int i = lane; i < s; i += 32) cfma_conj(acc, F[(long long)l * s + i], v[i]);
+        for (int i = lane; i < s; i += 32) cfma_conj(acc, Fq[(long long)l * s + i], v[i]);
         acc = warp_sum(acc);
         if (lane == 0) {
           c[l] = acc;
@@ -520,7 +536,7 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
         const int i = i0 + threadIdx.x / gT, sub = threadIdx.x % gT;
         Cx<R> acc(0, 0);
         if (i < s)
-          for (int l = sub; l < qc; l += gT) cfma(acc, F[(long long)l * s + i], c[l]);
+          for (int l = sub; l < qc; l += gT) cfma(acc, Fq[(long long)l * s + i], c[l]);
         for (int o = gT >> 1; o > 0; o >>= 1) acc += shfl_xor(acc, o);
         if (i < s && sub == 0) v[i] -= acc;
       }
@@ -531,7 +547,7 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
     nr = block_sum(nr, red);
     if (nr > Tiny<R>::dep * Tiny<R>::dep * nrm0 && nr > 0) {
       const R sn = sqrt(nr), is = R(1) / sn;
-      for (int i = threadIdx.x; i < s; i += blockDim.x) F[(long long)qc * s + i] = is * v[i];
+      for (int i = threadIdx.x; i < s; i += blockDim.x) Fq[(long long)qc * s + i] = is * v[i];
       if (threadIdx.x == 0) {
         Rm[(long long)qc * ld + j] = Cx<R>(sn, 0);
         s_qc = qc + 1;
@@ -540,6 +556,10 @@ __global__ void qr_cgs2(Geo g, Cx<R>* __restrict__ G_F, const int* __restrict__ 
       // dependent column: its projections were accumulated into R; drop the remainder
     }
     __syncthreads();
+  }
+  if (qsh) {
+    const int qc = s_qc;
+    for (int e = threadIdx.x; e < s * qc; e += blockDim.x) F[e] = Fq[e];
   }
   if (threadIdx.x == 0) { qcols[u] = s_qc; qmode[u] = 0; }
 }
@@ -719,7 +739,7 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Cb, cons
                            int* __restrict__ newrank, int smem_entries, R frz) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int a = g.list[blockIdx.x], b = a + 1, t = a >> 1;
-  const int qa = qcols[a], qb = qcols[b], w = G_rank[a];
+  const int qa = qcols[a], qb = qcols[b];
   // C (column-major qa x qb, ld qa) and, when both fit in the shared-memory plan, the
   // accumulated rotations W (column-major qb x qb, ld qb); otherwise W stays in Wb
   const bool w_shared = (long long)qa * qb + (long long)qb * qb <= smem_entries;
@@ -1137,7 +1157,10 @@ static int factor_impl(hsweep_s* h) {
   Cx<R>* Tx = (Cx<R>*)w->Tx;
   const int L = h->L, nn = h->nnodes, KCAP = w->KCAP, QCAP = w->QCAP;
   const size_t core_smem = (size_t)(2 * KCAP) * (2 * KCAP) * es + 32 * sizeof(R) + (2 * KCAP + 1) * sizeof(int) + 16;
-  const size_t qr_smem = (size_t)(h->tree.maxsz(1) + QCAP) * es + 32 * sizeof(R) + 16;
+  // QR: v, c and the reduction scratch, then as many entries of F_u as fit (226 KB in all)
+  const size_t qr_base = ((size_t)(h->tree.maxsz(1) + QCAP) * es + 32 * sizeof(R) + 15) & ~size_t(15);
+  const int qs_entries = qr_base < 226 * 1024 ? (int)((226 * 1024 - qr_base) / es) : 0;
+  const size_t qr_smem = qr_base + (size_t)qs_entries * es;
   // the Jacobi SVD's shared memory: C and, where it fits, the rotations W (up to 2 QCAP^2
   // entries; for large cores W stays in global memory)
   const size_t svd_tail = (size_t)(QCAP + 1) * sizeof(R) + (size_t)QCAP * sizeof(int) + 64;
@@ -1219,7 +1242,7 @@ static int factor_impl(hsweep_s* h) {
     if (nn_list <= 0) return HSWEEP_OK;
     Geo gl = g;
     gl.list = w->d_lists + node_off;
-    qr_cgs2<R><<<nn_list, 1024, qr_smem, st>>>(gl, G_F, w->G_rank, Rb, w->qcols, w->qmode);
+    qr_cgs2<R><<<nn_list, 1024, qr_smem, st>>>(gl, G_F, w->G_rank, Rb, w->qcols, w->qmode, qs_entries);
     Geo gp = g;
     gp.list = w->d_lists + pair_off;
     int rc = core_product(gp, np_list, kind);
@@ -1233,6 +1256,7 @@ static int factor_impl(hsweep_s* h) {
   };
 
   for (int m = 0; m < h->n; ++m) {
+    NvtxRange range("setup layer");
     m_cur = m;
     const Cx<R>* Tprev = m > 0 ? fac + (long long)(m - 1) * h->layer_stride : nullptr;
     const int* rprev = m > 0 ? h->d_rank + (long long)(m - 1) * nn : nullptr;
