@@ -650,11 +650,11 @@ def main():
                       "c64 H-factors, setup products and sweeps; inner GMRES in f32 arithmetic on f64 vectors; "
                       "f64 residuals, refinement and leaf inversions"),
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "N": n * n, "omega_over_2pi": omega / (2 * np.pi),
+            "config": {"workload": args.workload, "n": n, "N": n * n, "omega_over_2pi": omega / (2 * np.pi),
                        "pml": pml, "eps_H": eps, "nrhs": nrhs, "precision": "mixed", "tol": SOLVE_TOL,
                        "parallelism": "replica per GPU, sources sharded" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (1 GB RHS batch, factors %.2f GB)" % (
-                           stored * info["bytes_per_entry"] / 1e9)},
+                       "l2": "inputs larger than L2 (%.2f GB RHS batch, factors %.2f GB)" % (
+                           nrhs * n * n * 16 / 1e9, stored * info["bytes_per_entry"] / 1e9)},
             "setup_s": setup_s,
             "setup_tuning": setup_tuning,
             "ranks_per_depth": ranks,

@@ -332,6 +332,15 @@ __global__ void core_inverse(Geo g, int d, int m, const int* __restrict__ S_rank
   }
   const R tiny = (sizeof(R) == 8 ? R(1e-30) : R(1e-14)) * mx;   // on |pivot|^2
   bool bad = false;
+  // Gauss-Jordan in place, three block barriers per column: (1) pivot search and the
+  // pivot's inverse, (2) the row interchange with the normalisation of the pivot row, (3)
+  // the elimination of the other rows, each row owned by a group of gT lanes of one warp
+  // (the group reads its multiplier, synchronises, then updates its columns, the pivot
+  // column included)
+  int gT = 1;
+  while (gT < 32 && 2 * gT * n2 <= (int)blockDim.x) gT *= 2;
+  const int rows_per_pass = (int)blockDim.x / gT;
+  __shared__ Cx<R> s_ip;
   for (int kk = 0; kk < n2; ++kk) {
     if (threadIdx.x < 32) {
       // partial pivoting: warp 0 finds the largest |A[a][kk]|, a >= kk (ties: the smallest a)
@@ -350,34 +359,29 @@ __global__ void core_inverse(Geo g, int d, int m, const int* __restrict__ S_rank
         s_p = p;
         s_best = best;
         piv[kk] = p;
+        if (best > tiny) s_ip = cinv(A[p * n2 + kk]);
       }
     }
-    __syncthreads();
+    __syncthreads();                                                     // (1)
     if (!(s_best > tiny)) { bad = true; break; }
     const int p = s_p;
-    if (p != kk)
-      for (int b = threadIdx.x; b < n2; b += blockDim.x) {
-        Cx<R> tmp = A[kk * n2 + b]; A[kk * n2 + b] = A[p * n2 + b]; A[p * n2 + b] = tmp;
-      }
-    __syncthreads();
-    const Cx<R> ip = cinv(A[kk * n2 + kk]);
-    __syncthreads();
+    const Cx<R> ip = s_ip;
     for (int b = threadIdx.x; b < n2; b += blockDim.x) {
-      Cx<R> v = (b == kk) ? Cx<R>(1, 0) : A[kk * n2 + b];
-      A[kk * n2 + b] = v * ip;
+      const Cx<R> tk = A[kk * n2 + b], tp = A[p * n2 + b];
+      if (p != kk) A[p * n2 + b] = tk;
+      A[kk * n2 + b] = ((b == kk) ? Cx<R>(1, 0) : tp) * ip;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
-      const int a = e / n2, b = e % n2;
-      if (a == kk) continue;
-      const Cx<R> f = A[a * n2 + kk];
-      if (b == kk) continue;
-      A[e] -= f * A[kk * n2 + b];
+    __syncthreads();                                                     // (2)
+    for (int a0 = 0; a0 < n2; a0 += rows_per_pass) {
+      const int a = a0 + (int)threadIdx.x / gT, sub = (int)threadIdx.x % gT;
+      const bool live = a < n2 && a != kk;
+      const Cx<R> f = live ? A[a * n2 + kk] : Cx<R>(0, 0);
+      __syncwarp();
+      if (live)
+        for (int b = sub; b < n2; b += gT)
+          A[a * n2 + b] = (b == kk) ? -(f * ip) : A[a * n2 + b] - f * A[kk * n2 + b];
     }
-    __syncthreads();
-    for (int a = threadIdx.x; a < n2; a += blockDim.x)
-      if (a != kk) A[a * n2 + kk] = -(A[a * n2 + kk] * A[kk * n2 + kk]);
-    __syncthreads();
+    __syncthreads();                                                     // (3)
   }
   if (bad) {
     if (threadIdx.x == 0) report_error(status, HSWEEP_ERR_NUMERIC, m);
