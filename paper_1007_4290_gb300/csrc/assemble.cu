@@ -47,24 +47,25 @@ __global__ void assemble_kernel(int n, double h, double eta, double pref, double
   diag[p] = k2 - (((e_l + e_r) + n_l) + n_r);
 }
 
-// y[s] = A x[s] for right-hand sides s0 .. s0 + 7: one thread per node, the five
-// coefficients loaded once, the 8 x 5 neighbour values of all eight right-hand sides in
-// flight together
+// y[s] = A x[s] (f null) or the residual y[s] = f[s] - A x[s], for right-hand sides
+// s0 .. s0 + 7: one thread per node, the five coefficients loaded once (negated for the
+// residual), the 8 x 5 neighbour values of all eight right-hand sides in flight together
 constexpr int kMvRhs = 8;
 template <typename T>
 __global__ void matvec_kernel(int n, long long N, int nrhs, const c128* __restrict__ diag,
                               const c128* __restrict__ east, const c128* __restrict__ north,
-                              const c128* __restrict__ x, c128* __restrict__ y) {
+                              const c128* __restrict__ x, c128* __restrict__ y, const c128* __restrict__ f) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int j = (int)(p / n), i = (int)(p - (long long)j * n);
   const int s0 = blockIdx.y * kMvRhs;
   const c128 zero(0.0, 0.0);
-  const Cx<T> d = cvt<T>(diag[p]);
-  const Cx<T> el = cvt<T>(i > 0 ? east[(long long)j * (n + 1) + i] : zero);
-  const Cx<T> er = cvt<T>(i < n - 1 ? east[(long long)j * (n + 1) + i + 1] : zero);
-  const Cx<T> nl = cvt<T>(j > 0 ? north[(long long)j * n + i] : zero);
-  const Cx<T> nr = cvt<T>(j < n - 1 ? north[(long long)(j + 1) * n + i] : zero);
+  const T sg = f ? T(-1) : T(1);
+  const Cx<T> d = sg * cvt<T>(diag[p]);
+  const Cx<T> el = sg * cvt<T>(i > 0 ? east[(long long)j * (n + 1) + i] : zero);
+  const Cx<T> er = sg * cvt<T>(i < n - 1 ? east[(long long)j * (n + 1) + i + 1] : zero);
+  const Cx<T> nl = sg * cvt<T>(j > 0 ? north[(long long)j * n + i] : zero);
+  const Cx<T> nr = sg * cvt<T>(j < n - 1 ? north[(long long)(j + 1) * n + i] : zero);
   const long long pl = i > 0 ? p - 1 : p, pr = i < n - 1 ? p + 1 : p;
   const long long pd = j > 0 ? p - n : p, pu = j < n - 1 ? p + n : p;
   Cx<T> v[kMvRhs][5];
@@ -86,7 +87,8 @@ __global__ void matvec_kernel(int n, long long N, int nrhs, const c128* __restri
 #pragma unroll
     for (int u = 0; u < kMvRhs; ++u) {
       if (s0 + u < nrhs) {
-        T re = d.re * v[u][0].re, im = d.re * v[u][0].im;
+        const Cx<T> f0 = f ? cvt<T>(f[(long long)(s0 + u) * N + p]) : Cx<T>(0, 0);
+        T re = fma(d.re, v[u][0].re, f0.re), im = fma(d.re, v[u][0].im, f0.im);
         re = fma(el.re, v[u][1].re, re); im = fma(el.re, v[u][1].im, im);
         re = fma(er.re, v[u][2].re, re); im = fma(er.re, v[u][2].im, im);
         re = fma(nl.re, v[u][3].re, re); im = fma(nl.re, v[u][3].im, im);
@@ -99,7 +101,8 @@ __global__ void matvec_kernel(int n, long long N, int nrhs, const c128* __restri
 #pragma unroll
   for (int u = 0; u < kMvRhs; ++u) {
     if (s0 + u < nrhs) {
-      Cx<T> acc = d * v[u][0];
+      Cx<T> acc = f ? cvt<T>(f[(long long)(s0 + u) * N + p]) : Cx<T>(0, 0);
+      cfma(acc, d, v[u][0]);
       cfma(acc, el, v[u][1]);
       cfma(acc, er, v[u][2]);
       cfma(acc, nl, v[u][3]);
@@ -123,21 +126,29 @@ int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides, c128* d
   return HSWEEP_OK;
 }
 
-int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp) {
+static int matvec_launch(hsweep_s* h, const c128* x, c128* y, const c128* f, int nrhs, bool lowp) {
   if (nrhs <= 0) return HSWEEP_OK;
   dim3 grid(div_up(h->N, 256), div_up(nrhs, kMvRhs));
   if (lowp)
     matvec_kernel<float><<<grid, 256, 0, h->stream>>>(h->n, (long long)h->N, nrhs, h->d_diag, h->d_east,
-                                                      h->d_north, x, y);
+                                                      h->d_north, x, y, f);
   else
     matvec_kernel<double><<<grid, 256, 0, h->stream>>>(h->n, (long long)h->N, nrhs, h->d_diag, h->d_east,
-                                                       h->d_north, x, y);
+                                                       h->d_north, x, y, f);
   h->nlaunch += 1;
   HSW_CUDA(cudaGetLastError());
   return HSWEEP_OK;
 }
 
-int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs) { return hsw_matvec_prec(h, x, y, nrhs, false); }
+int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp) {
+  return matvec_launch(h, x, y, nullptr, nrhs, lowp);
+}
+
+int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs) { return matvec_launch(h, x, y, nullptr, nrhs, false); }
+
+int hsw_residual(hsweep_s* h, const c128* f, const c128* u, c128* r, int nrhs) {
+  return matvec_launch(h, u, r, f, nrhs, false);
+}
 
 namespace {
 

@@ -87,6 +87,7 @@ struct hsweep_s {
   // CTA}; cleared whenever the packed factors change
   std::vector<std::array<long long, 8>> team_plans;
   int rank_max = 0;
+  std::vector<int> rank_max_depth;       // per depth d = 0..L: the largest rank over all layers
   bool pack_valid = false;
 
   int* d_status = nullptr;     // [2]
@@ -142,6 +143,8 @@ int hsw_assemble(hsweep_s* h, double pml_C, int pml_form, int pml_sides, c128* d
 // Dirichlet data b on one side as a forcing term on the adjacent layer (Section 2.5)
 int hsw_boundary_rhs(hsweep_s* h, int side, const c128* b, c128* f, int nrhs);
 int hsw_matvec(hsweep_s* h, const c128* x, c128* y, int nrhs);
+// r = f - A u (FP64), one pass
+int hsw_residual(hsweep_s* h, const c128* f, const c128* u, c128* r, int nrhs);
 // the same product with FP32 arithmetic (lowp) on the FP64 vectors
 int hsw_matvec_prec(hsweep_s* h, const c128* x, c128* y, int nrhs, bool lowp);
 // noalloc.cu: look up the fixed scratch array on the current (the handle's) device

@@ -58,8 +58,13 @@ __global__ void dots_kernel(const c128* const* __restrict__ V, int nv, int nt, c
     for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) {
       const Cx<T> wp = cvt<T>(ws[p]);
 #pragma unroll
-      for (int i = 0; i < kDotChunk; ++i)
-        if (i < nc) cfma_conj(acct[i], cvt<T>(vs[i][p]), wp);
+      for (int i = 0; i < kDotChunk; ++i) {
+        if (i0 + i < nv) {
+          if (i < nc) cfma_conj(acct[i], cvt<T>(vs[i][p]), wp);
+        } else if (i < nc) {
+          acct[i].re += abs2(wp);      // the squared norm: two multiply-adds, not four
+        }
+      }
     }
     c128 acc[kDotChunk];
 #pragma unroll
@@ -115,15 +120,19 @@ __global__ void reduce_partials(const c128* __restrict__ partial, int B, c128* _
 }
 
 // y[s] += sign * sum_i coef[s * ldc + i] * V_i[s]; the basis pointers and coefficients of
-// the block's right-hand side are staged in shared memory, kAxpyMax at a time
+// the block's right-hand side are staged in shared memory, kAxpyMax at a time.  With out
+// set (nv <= kAxpyMax), the result divided by nrm[s] goes to out[s] instead of y (zero
+// when nrm[s] = 0): the projection and the normalisation of an Arnoldi step in one pass.
 constexpr int kAxpyMax = 64;
 template <typename T>
 __global__ void axpy_multi(const c128* const* __restrict__ V, int nv, const c128* __restrict__ coef, int ldc,
-                           double sign, c128* __restrict__ y, long long N) {
+                           double sign, c128* __restrict__ y, long long N, const double* __restrict__ nrm = nullptr,
+                           c128* __restrict__ out = nullptr) {
   const int s = blockIdx.y;
   __shared__ const c128* sv[kAxpyMax];
   __shared__ Cx<T> sc[kAxpyMax];
   c128* ys = y + (long long)s * N;
+  const T inv = (out && nrm[s] > 0) ? T(1.0 / nrm[s]) : T(0);
   for (int i0 = 0; i0 < nv; i0 += kAxpyMax) {
     const int nc = min(kAxpyMax, nv - i0);
     __syncthreads();
@@ -135,7 +144,8 @@ __global__ void axpy_multi(const c128* const* __restrict__ V, int nv, const c128
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
       Cx<T> acc = cvt<T>(ys[p]);
       for (int i = 0; i < nc; ++i) cfma(acc, sc[i], cvt<T>(sv[i][p]));
-      ys[p] = cvt<double>(acc);
+      if (out) out[(long long)s * N + p] = cvt<double>(inv * acc);
+      else ys[p] = cvt<double>(acc);
     }
   }
 }
@@ -155,11 +165,6 @@ __global__ void copy_words(const unsigned long long* __restrict__ src, unsigned 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
-// r = f - y
-__global__ void sub_kernel(const c128* __restrict__ f, const c128* __restrict__ y, c128* __restrict__ r, long long n) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
-    r[p] = f[p] - y[p];
-}
 
 }  // namespace
 
@@ -168,7 +173,7 @@ struct KrylovWork {
   std::vector<c128*> V;        // basis vectors, each [nrhs_cap][N]
   c128** d_V = nullptr;        // device copy of the pointer table
   int d_V_cap = 0;
-  c128 *r = nullptr, *z = nullptr, *w = nullptr, *t = nullptr, *d = nullptr;
+  c128 *r = nullptr, *z = nullptr, *w = nullptr, *t = nullptr;
   c128* partial = nullptr;
   c128* dots = nullptr;        // [nrhs][vmax]
   c128* coef = nullptr;        // [nrhs][vmax]
@@ -179,10 +184,10 @@ struct KrylovWork {
   // kernel on the handle's stream instead of the copy engines, so that bulk transfers a
   // caller runs beside the solve on another stream (the next batch's right-hand sides, the
   // previous batch's solutions) never hold up its per-iteration exchanges.  Regions (bytes):
-  // coefficients up, norms up, one pointer up, the basis table up, results down.
+  // coefficients up, norms up, the basis table up, results down.
   unsigned char* mbox_h = nullptr;
   unsigned char* mbox_d = nullptr;
-  size_t o_coef = 0, o_nrm = 0, o_tbl = 0, o_vtab = 0, o_down = 0, mbox_bytes = 0;
+  size_t o_coef = 0, o_nrm = 0, o_vtab = 0, o_down = 0, mbox_bytes = 0;
 };
 
 // bytes (a multiple of 8) from host src to device dst through the mailbox region `region`;
@@ -217,7 +222,7 @@ void hsw_krylov_free(hsweep_s* h) {
   if (!h->kw) return;
   KrylovWork* k = h->kw;
   for (c128* p : k->V) hsw_release(h, p);
-  void* ptrs[] = {k->d_V, k->r, k->z, k->w, k->t, k->d, k->partial, k->dots, k->coef, k->nrm};
+  void* ptrs[] = {k->d_V, k->r, k->z, k->w, k->t, k->partial, k->dots, k->coef, k->nrm};
   for (void* p : ptrs) hsw_release(h, p);
   if (k->mbox_h) cudaFreeHost(k->mbox_h);
   delete k;
@@ -236,7 +241,7 @@ static int krylov_reserve(hsweep_s* h, int nrhs) {
   int rc;
 #define A(p, bytes) do { rc = hsw_alloc(h, (void**)&(p), (size_t)(bytes)); if (rc) return rc; } while (0)
   A(k->d_V, vmax * sizeof(c128*));
-  A(k->r, vb); A(k->z, vb); A(k->w, vb); A(k->t, vb); A(k->d, vb);
+  A(k->r, vb); A(k->z, vb); A(k->w, vb); A(k->t, vb);
   A(k->partial, (size_t)nrhs * vmax * kRedBlocks * sizeof(c128));
   A(k->dots, (size_t)nrhs * vmax * sizeof(c128));
   A(k->coef, (size_t)nrhs * vmax * sizeof(c128));
@@ -247,9 +252,8 @@ static int krylov_reserve(hsweep_s* h, int nrhs) {
   const size_t vt = ((size_t)vmax * sizeof(c128*) + 255) / 256 * 256;
   k->o_coef = 0;
   k->o_nrm = cb;
-  k->o_tbl = cb + nb;
-  k->o_vtab = cb + nb + 256;
-  k->o_down = cb + nb + 256 + vt;
+  k->o_vtab = cb + nb;
+  k->o_down = cb + nb + vt;
   k->mbox_bytes = k->o_down + cb;
   void* hp = nullptr;
   if (cudaHostAlloc(&hp, k->mbox_bytes, cudaHostAllocMapped) != cudaSuccess) {
@@ -321,10 +325,11 @@ static dim3 vec_grid(hsweep_s* h, int nrhs) {
   return dim3((unsigned)blocks, nrhs);
 }
 
-// Inner GMRES on (M A) d = z, x0 = 0.  eta[s]: relative tolerance on ||z_s||; active[s]
+// Inner GMRES on (M A) d = z, x0 = 0, adding its solution d to u (the right-hand sides
+// not active are left unchanged).  eta[s]: relative tolerance on ||z_s||; active[s]
 // marks the right-hand sides being solved.  Adds the Arnoldi steps to iters.
 static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<double>& znrm,
-                       const std::vector<double>& eta, std::vector<char>& active, c128* d, std::vector<int>& iters,
+                       const std::vector<double>& eta, std::vector<char>& active, c128* u, std::vector<int>& iters,
                        std::vector<double>& est) {
   KrylovWork* k = h->kw;
   const int maxit = h->opt.gmres_max_it;
@@ -370,7 +375,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     // only when some right-hand side lost more than half of its squared norm
     std::vector<cd> hcol((size_t)nrhs * (j + 1), cd(0));
     std::vector<double> wn(nrhs, 0.0);
-    bool second = false;
+    bool second = false, fused = false;
     {
       if ((rc = batched_dots(h, 0, j + 1, k->w, nrhs, hd, lowp, true))) return rc;
       std::vector<cd> h1((size_t)nrhs * (j + 1));
@@ -387,8 +392,15 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
       }
       for (size_t e = 0; e < h1.size(); ++e) hcol[e] += h1[e];
       if ((rc = mbox_up(h, k->o_coef, h1.data(), k->coef, h1.size() * sizeof(c128)))) return rc;
-      if (lowp) axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
-      else axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N);
+      // without a second pass the norm is known already: project and normalise in one pass
+      fused = !second && j + 1 <= kAxpyMax;
+      if (fused && (rc = mbox_up(h, k->o_nrm, wn.data(), k->nrm, nrhs * sizeof(double)))) return rc;
+      const double* fn = fused ? k->nrm : nullptr;
+      c128* fo = fused ? vn : nullptr;
+      if (lowp)
+        axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N, fn, fo);
+      else
+        axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, j + 1, k->coef, j + 1, -1.0, k->w, N, fn, fo);
       h->nlaunch += 1;
     }
     if (second) {
@@ -400,10 +412,12 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
       h->nlaunch += 1;
       if ((rc = norms(h, k->w, nrhs, wn, lowp))) return rc;
     }
-    if ((rc = mbox_up(h, k->o_nrm, wn.data(), k->nrm, nrhs * sizeof(double)))) return rc;
-    if (lowp) scale_kernel<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
-    else scale_kernel<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
-    h->nlaunch += 1;
+    if (!fused) {
+      if ((rc = mbox_up(h, k->o_nrm, wn.data(), k->nrm, nrhs * sizeof(double)))) return rc;
+      if (lowp) scale_kernel<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
+      else scale_kernel<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->w, k->nrm, vn, N);
+      h->nlaunch += 1;
+    }
     for (int s = 0; s < nrhs; ++s) {
       if (!run[s]) continue;
       cd* Hs = H[s].data();
@@ -428,7 +442,8 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
       if (est[s] <= eta[s] || wn[s] == 0.0 || r == 0.0) run[s] = 0;
     }
   }
-  // d = sum_i y_i v_i with H y = g (upper-triangular back substitution per RHS)
+  // u += sum_i y_i v_i with H y = g (upper-triangular back substitution per RHS; y = 0
+  // for the right-hand sides not active)
   std::vector<cd> Y((size_t)nrhs * std::max(1, maxit), cd(0));
   int kmax = 0;
   for (int s = 0; s < nrhs; ++s) {
@@ -442,14 +457,13 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
       Y[(size_t)s * maxit + i] = Hs[i * maxit + i] != cd(0) ? acc / Hs[i * maxit + i] : cd(0);
     }
   }
-  HSW_CUDA(cudaMemsetAsync(d, 0, (size_t)nrhs * N * sizeof(c128), h->stream));
   if (kmax > 0) {
     std::vector<cd> Yc((size_t)nrhs * kmax, cd(0));
     for (int s = 0; s < nrhs; ++s)
       for (int i = 0; i < kmax; ++i) Yc[(size_t)s * kmax + i] = Y[(size_t)s * maxit + i];
     if ((rc = mbox_up(h, k->o_coef, Yc.data(), k->coef, Yc.size() * sizeof(c128)))) return rc;
-    if (lowp) axpy_multi<float><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
-    else axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, d, N);
+    // u is FP64 in every mode: the update runs in FP64
+    axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(k->d_V, kmax, k->coef, kmax, 1.0, u, N);
     h->nlaunch += 1;
     HSW_CUDA(cudaGetLastError());
   }
@@ -483,9 +497,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
     if (outer == 0 && u_zero) {
       zn = Mfn;      // k->z still holds M f
     } else {
-      if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
-      sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
-      h->nlaunch += 1;
+      if ((rc = hsw_residual(h, f, u, k->r, nrhs))) return rc;
       if ((rc = hsw_apply(h, k->r, k->z, nrhs))) return rc;
       if ((rc = norms(h, k->z, nrhs, zn, lowp))) return rc;
     }
@@ -503,19 +515,8 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
       eta[s] = mixed ? std::max(0.5 * need, 4e-6) : 0.9 * need;
     }
     if (all_done) break;
-    if ((rc = gmres_inner(h, k->z, nrhs, zn, eta, active, k->d, iters, est))) return rc;
     // u += d for the active right-hand sides
-    {
-      std::vector<std::complex<double>> one((size_t)nrhs, 0.0);
-      for (int s = 0; s < nrhs; ++s) one[s] = active[s] ? 1.0 : 0.0;
-      const c128* tbl[1] = {k->d};
-      if ((rc = mbox_up(h, k->o_tbl, tbl, k->dots, sizeof(c128*)))) return rc;
-      if ((rc = mbox_up(h, k->o_coef, one.data(), k->coef, nrhs * sizeof(c128)))) return rc;
-      axpy_multi<double><<<vec_grid(h, nrhs), 256, 0, h->stream>>>(reinterpret_cast<const c128* const*>(k->dots), 1,
-                                                           k->coef, 1, 1.0, u, N);
-      h->nlaunch += 1;
-      HSW_CUDA(cudaGetLastError());
-    }
+    if ((rc = gmres_inner(h, k->z, nrhs, zn, eta, active, u, iters, est))) return rc;
     if (!mixed) {
       // FP64: the inner residual estimate is the FP64 one; stop when it met the tolerance
       bool ok = true;
@@ -535,9 +536,7 @@ int hsw_solve(hsweep_s* h, const c128* f, c128* u, int nrhs, double tol, int* it
     }
   }
   // final FP64 residual
-  if ((rc = hsw_matvec(h, u, k->t, nrhs))) return rc;
-  sub_kernel<<<1216, 256, 0, h->stream>>>(f, k->t, k->r, (long long)nrhs * N);
-  h->nlaunch += 1;
+  if ((rc = hsw_residual(h, f, u, k->r, nrhs))) return rc;
   std::vector<double> rn;
   if ((rc = norms(h, k->r, nrhs, rn))) return rc;
   if (!all_done && mixed) {

@@ -100,6 +100,13 @@ int hsw_pack(hsweep_s* h, int m0, int m1) {
   }
   h->rank_max = 0;
   for (int v : rk) h->rank_max = std::max(h->rank_max, v);
+  h->rank_max_depth.assign(h->L + 1, 0);
+  for (int m = 0; m < h->n; ++m)
+    for (int v = 2; v < h->nnodes; ++v) {
+      int d = 0;
+      while ((2 << d) <= v) ++d;
+      h->rank_max_depth[d] = std::max(h->rank_max_depth[d], rk[(size_t)m * h->nnodes + v]);
+    }
   h->pack_valid = true;
   return HSWEEP_OK;
 }

@@ -68,6 +68,8 @@ __device__ __forceinline__ void upk2(u64 v, float& lo, float& hi) {
 __device__ __forceinline__ void fma2(u64& acc, u64 a, u64 b) {
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
+// bring the 128-byte line at p into L2 (no register result, nothing waits for it)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Tagged partial sums in L2.  Naturally aligned 8-byte accesses are single-copy atomic,
 // so one tag bit (bit 0, the lowest mantissa bit of the real part in complex64, of each
@@ -216,13 +218,16 @@ struct TeamArgs {
                                 // (kWaitLimit unless a test shortens it; the waits for this
                                 // CTA's own bulk copies always allow kWaitLimit)
   int withhold;                 // test only: this CTA never publishes its partial sums (-1: none)
+  int qcapd[16];                // per depth: the largest rank over all layers (capacity of the
+                                // shared q slots; the exchanged slots below it are rewritten
+                                // every step)
   // shared-memory plan (byte offsets)
-  unsigned o_stage[2], o_rowoff, o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_etab[2], o_x[2],
+  unsigned o_stage[2], o_rowoff[2], o_trk[3], o_ro[3], o_lo, o_sz, o_leafnode, o_dtab, o_wdesc, o_etab[2], o_x[2],
       o_qanc, o_qloc, o_mbar, o_flags;
 };
 
 // per-depth table columns in shared memory (16 ints each)
-enum { DT_NODES = 0, DT_QCAP = 16, DT_WSTART = 32, DT_QBASE = 48, DT_SIZE = 64 };
+enum { DT_NODES = 0, DT_QCAP = 16, DT_WSTART = 32, DT_QBASE = 48, DT_QANC = 64, DT_SIZE = 80 };
 
 // Reduction of one warp-item: lane (column k, row subset rl) sums rows rb + rl,
 // rb + rl + 4, ... < re of column k for all G right-hand sides.
@@ -297,17 +302,19 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
   const int lo_c = s_lo[vc], ns = s_sz[vc];
   if (tid == 0) {
     // reduction warp-items per depth: (node, chunk of kKW columns); ancestors first
-    int wsum = 0, qb = 0;
+    int wsum = 0, qb = 0, qa = 0;
     for (int d = 1; d <= L; ++d) {
       const int rows = d <= dC ? ns : (n + (1 << d) - 1) >> d;
       const int nodes = d <= dC ? 1 : (1 << (d - dC));
-      const int qcap = d <= dC ? a.rcap : min(rows, a.rcap);
+      const int qcap = d <= dC ? a.qcapd[d] : min(rows, a.qcapd[d]);
       dt[DT_NODES + d] = nodes;
       dt[DT_QCAP + d] = qcap;
       dt[DT_WSTART + d] = wsum;
       wsum += nodes * ((qcap + kKW - 1) / kKW);
       dt[DT_QBASE + d] = qb;
+      dt[DT_QANC + d] = qa;
       if (d > dC) qb += nodes * qcap * GS;
+      else qa += qcap * GS;
     }
     dt[DT_WSTART + L + 1] = wsum;
     int* wdesc = reinterpret_cast<int*>(sm + a.o_wdesc);
@@ -361,20 +368,20 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
       }
     }
   };
-  // all threads: from the ranks and record offsets in table slot slot3, the offset of
-  // every row of every block of that step's record (rowoff), and per (slab leaf, depth)
-  // the rank and the shared-memory vector block the expansion multiplies it with (etab
-  // buffer eb)
-  auto build_tables = [&](int slot3, int eb) {
+  // threads w0, w0 + wn, ...: from the ranks and record offsets in table slot slot3, the
+  // offset of every row of every block of that step's record (rowoff buffer rb), and per
+  // (slab leaf, depth) the rank and the shared-memory vector block the expansion multiplies
+  // it with (etab buffer eb)
+  auto build_tables = [&](int slot3, int eb, int rb, int w0, int wn) {
     const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[slot3]);
     const long long* sro = reinterpret_cast<const long long*>(sm + a.o_ro[slot3]);
-    int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff);
+    int* rowoff = reinterpret_cast<int*>(sm + a.o_rowoff[rb]);
     int* erk = reinterpret_cast<int*>(sm + a.o_etab[eb]);
     int* evo = erk + nl * L1;
     auto rank_at = [&](int lam, int d) {
       return d <= dC ? trk[d - 1] : trk[dC + (1 << (d - dC)) - 2 + ((lam >> (L - d)) - (vc << (d - dC)))];
     };
-    for (int e = tid; e < ns * L1; e += NT) {
+    for (int e = w0; e < ns * L1; e += wn) {
       const int i = e % ns, d = e / ns;
       const int lam = s_leafnode[i];
       const int j = lam - lam0;
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
       }
       rowoff[d * SM + i] = o;
     }
-    for (int e = tid; e < nl * L1; e += NT) {
+    for (int e = w0; e < nl * L1; e += wn) {
       const int j = e / L1, d = e % L1;
       const int lam = lam0 + j;
       int r, vo = 0;
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
       } else {
         r = rank_at(lam, d);
         if (d <= dC) {
-          vo = (int)a.o_qanc + (int)sizeof(Cx<R>) * ((d - 1) * a.rcap * GS);
+          vo = (int)a.o_qanc + (int)sizeof(Cx<R>) * dt[DT_QANC + d];
         } else {
           const int jn = (lam >> (L - d)) - (vc << (d - dC));
           vo = (int)a.o_qloc + (int)sizeof(Cx<R>) * (dt[DT_QBASE + d] + ((jn ^ 1) * dt[DT_QCAP + d]) * GS);
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
     produce(0, 0, 0);
   }
   __syncthreads();
-  if (total_steps > 0) build_tables(0, 0);
+  if (total_steps > 0) build_tables(0, 0, 0, tid, NT);
   __syncthreads();
 
   int issued = total_steps > 0 ? 1 : 0;   // bulk copies issued (steps 0 .. issued-1)
@@ -473,7 +480,7 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
       }
     }
     const Cx<R>* st = reinterpret_cast<const Cx<R>*>(sm + a.o_stage[slot]);
-    const int* rowoff = reinterpret_cast<const int*>(sm + a.o_rowoff);
+    const int* rowoff = reinterpret_cast<const int*>(sm + a.o_rowoff[t & 1]);
     const int* trk = reinterpret_cast<const int*>(sm + a.o_trk[slot3]);
     const int* wdesc = reinterpret_cast<const int*>(sm + a.o_wdesc);
     const int* erk = reinterpret_cast<const int*>(sm + a.o_etab[slot]);
@@ -537,14 +544,36 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
     const bool ok1 = *s_fail == 0;
     if (warp == 0 && ok1 && t + 1 < total_steps) {
       const int s1 = s + 1 == nsteps ? 0 : s + 1;
-      cp_async_wait0();      // the tables of step t + 1
-      __syncwarp();
       produce(s1, inc3(slot3), slot ^ 1);
       if (t + 2 < total_steps) {
         load_tables(s1 + 1 == nsteps ? 0 : s1 + 1, inc3(inc3(slot3)));
         cp_async_commit();
       }
       issued = t + 2;
+      // the global inputs of step t + 1's update (the coupling row, and per right-hand side
+      // the next layer's rows of r or the cached rows of w) into L2 a step ahead: they are
+      // read once per launch, from HBM, at the end of a step
+      {
+        const bool fwd1 = s1 < n;
+        const int m1 = fwd1 ? s1 : 2 * n - 2 - s1;
+        const int g01 = (s1 == 0 ? grp + a.nteams : grp) * G;
+        const int gc1 = max(0, min(G, a.nrhs - g01));
+        const int mn1 = (fwd1 && m1 < n - 1) ? m1 + 1 : m1;
+        const bool rin = fwd1 && m1 < n - 1;
+        const int lines_c = (ns * (int)sizeof(c128) + 127) >> 7;
+        const int lines_v = rin ? lines_c : (!fwd1 ? (ns * (int)sizeof(Cx<R>) + 127) >> 7 : 0);
+        const int tot = lines_c + gc1 * lines_v;
+        for (int q = lane; q < tot; q += 32) {
+          if (q < lines_c) {
+            prefetch_l2(reinterpret_cast<const unsigned char*>(a.north + (long long)mn1 * n + lo_c) + 128 * q);
+          } else {
+            const int g = (q - lines_c) / lines_v, l = (q - lines_c) % lines_v;
+            const long long row = (long long)(g01 + g) * a.N;
+            if (rin) prefetch_l2(reinterpret_cast<const unsigned char*>(a.r + row + (long long)(m1 + 1) * n + lo_c) + 128 * l);
+            else prefetch_l2(reinterpret_cast<const unsigned char*>(a.w + row + (long long)m1 * n + lo_c) + 128 * l);
+          }
+        }
+      }
     }
     // ancestors' partial sums on tensor cores: warp-items (depth d, 16 columns), the
     // columns as two n-tiles, the slab's rows as the k dimension
@@ -599,6 +628,9 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
       if (tc) reduce_anc_tc();
       else reduce_items(0, dt[DT_WSTART + dC + 1], 0);
       reduce_items(dt[DT_WSTART + dC + 1], dt[DT_WSTART + L + 1], 1);
+      // the row offsets and block tables of step t + 1 (buffers step t does not read),
+      // while the other CTAs' partial sums are on their way
+      if (t + 1 < total_steps) build_tables(inc3(slot3), slot ^ 1, (t + 1) & 1, tid, NT);
       constexpr int GJ = sizeof(R) == 4 ? 3 : 1;
       const int rg = a.rcap * G;
       const int tot = dC * rg;
@@ -668,7 +700,7 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
           }
           const int d = it / rg + 1;
           const int kg = it - (d - 1) * rg;
-          qanc[(d - 1) * a.rcap * GS + (kg / G) * GS + kg % G] = acc;
+          if (kg / G < dt[DT_QCAP + d]) qanc[dt[DT_QANC + d] + (kg / G) * GS + kg % G] = acc;
         }
       }
     }
@@ -690,7 +722,7 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
           const int rA = 16 * warp + g, rB = rA + 8;
           for (int d = 1; d <= dC; ++d) {
             const int r = trk[d - 1];
-            const Cx<float>* q = qanc + (d - 1) * a.rcap * GS;
+            const Cx<float>* q = qanc + dt[DT_QANC + d];
             const float* Fa = reinterpret_cast<const float*>(st + (rA < ns ? rowoff[d * SM + rA] : 0)) + pp;
             const float* Fb = reinterpret_cast<const float*>(st + (rB < ns ? rowoff[d * SM + rB] : 0)) + pp;
             for (int k0 = 0; k0 < r; k0 += 4) {
@@ -827,8 +859,10 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
         }
       }
     }
-    if (t + 1 < total_steps) build_tables(inc3(slot3), slot ^ 1);
     if (tid == 0) { s_ctr[0] = 0; s_ctr[1] = 0; }
+    // the tables of step t + 2 (cp.async, issued at the start of this step) land before the
+    // barrier, so that step t + 1 can build its successor's row offsets from them
+    if (warp == 0) cp_async_wait0();
     __syncthreads();
     if (++s == nsteps) { s = 0; grp += a.nteams; }
     slot3 = inc3(slot3);
@@ -872,25 +906,28 @@ static size_t plan_team(const hsweep_s* h, int dC, int G, TeamArgs<R>& a, int nt
   size_t o = 0;
   const size_t stage = al((size_t)h->slab_bytes_max[dC], 128);
   for (int b = 0; b < 2; ++b) { a.o_stage[b] = (unsigned)o; o += stage; }
-  a.o_rowoff = (unsigned)o; o += al((size_t)(L + 1) * slab_max * sizeof(int), 16);
+  for (int b = 0; b < 2; ++b) { a.o_rowoff[b] = (unsigned)o; o += al((size_t)(L + 1) * slab_max * sizeof(int), 16); }
   for (int b = 0; b < 3; ++b) { a.o_trk[b] = (unsigned)o; o += al((size_t)(dC + 2 * nl) * sizeof(int), 16); }
   for (int b = 0; b < 3; ++b) { a.o_ro[b] = (unsigned)o; o += al((size_t)(nl + 1) * sizeof(long long), 16); }
   a.o_lo = (unsigned)o; o += al(h->nnodes * sizeof(int), 16);
   a.o_sz = (unsigned)o; o += al(h->nnodes * sizeof(int), 16);
   a.o_leafnode = (unsigned)o; o += al(slab_max * sizeof(int), 16);
   a.o_dtab = (unsigned)o; o += al(DT_SIZE * sizeof(int), 16);
-  long long wtot = 0, qloc = 0;
+  long long wtot = 0, qloc = 0, qanc = 0;
+  for (int d = 0; d < 16; ++d)
+    a.qcapd[d] = d <= L && d < (int)h->rank_max_depth.size() ? std::min(rcap, h->rank_max_depth[d]) : 0;
   for (int d = 1; d <= L; ++d) {
     const int rows = d <= dC ? slab_max : h->tree.maxsz(d);
     const int nodes = d <= dC ? 1 : (1 << (d - dC));
-    const int qcap = d <= dC ? rcap : std::min(rows, rcap);
+    const int qcap = d <= dC ? a.qcapd[d] : std::min(rows, a.qcapd[d]);
     wtot += (long long)nodes * ((qcap + kKW - 1) / kKW);
     if (d > dC) qloc += (long long)nodes * qcap * GS;
+    else qanc += (long long)qcap * GS;
   }
   a.o_wdesc = (unsigned)o; o += al((size_t)wtot * sizeof(int), 16);
   for (int b = 0; b < 2; ++b) { a.o_etab[b] = (unsigned)o; o += al((size_t)2 * nl * (L + 1) * sizeof(int), 16); }
   for (int b = 0; b < 2; ++b) { a.o_x[b] = (unsigned)o; o += al((size_t)slab_max * GS * es, 16); }
-  a.o_qanc = (unsigned)o; o += al((size_t)std::max(1, dC) * rcap * GS * es, 16);
+  a.o_qanc = (unsigned)o; o += al((size_t)std::max(1LL, qanc) * es, 16);
   a.o_qloc = (unsigned)o; o += al((size_t)std::max(1LL, qloc) * es, 16);
   a.o_mbar = (unsigned)o; o += 16;
   a.o_flags = (unsigned)o; o += 16;
