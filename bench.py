@@ -68,6 +68,33 @@ def sweep_work(h, n, nrhs, elem_bytes):
     return flops, fac_bytes + vec_bytes, sum(lr) + n * leaf_e
 
 
+def strong_sweep_work(n, R, nrhs, elem_bytes):
+    """The same for the sweep on the strongly admissible format (sweep_strong.cu): per layer
+    step and row, its near-field entries (its leaf and the neighbouring leaves) once and
+    the R entries of every block of its clusters' interaction lists twice (reduction and
+    expansion) per RHS; the records, stored entries included, are read once per step."""
+    L, sz = _tree_sizes(n)
+    nleaves = 1 << L
+    near = far = stored = 0
+    for j in range(nleaves):
+        lam = nleaves + j
+        s = sz[lam]
+        sl = sz[lam - 1] if j > 0 else 0
+        sr = sz[lam + 1] if j < nleaves - 1 else 0
+        near += s * (s + sl + sr)
+        stored += (s * ((s + sl + sr + 3 * R * (L - 1)) | 1) + 1) // 2 * 2
+        for d in range(2, L + 1):
+            c = lam >> (L - d)
+            cl = c - (1 << d)
+            offs = (-3, -2, 2) if cl & 1 else (-2, 2, 3)
+            far += s * R * sum(1 for o in offs if 0 <= cl + o < (1 << d))
+    steps = 2 * n - 1
+    flops = 8.0 * nrhs * steps * (near + 2 * far)
+    fac_bytes = steps * stored * elem_bytes
+    vec_bytes = nrhs * n * n * (16 + 16 + 2 * elem_bytes)
+    return flops, fac_bytes + vec_bytes, n * stored
+
+
 # DRAM bytes (read + write) of one sweep launch, from ncu captures summarised in profiles/,
 # keyed by workload and right-hand sides, with the SHA-256 of the kernel source they were
 # taken on: a changed kernel reports null instead of a stale number.
@@ -838,9 +865,14 @@ def run_parts(args):
             h.apply(R, Z)
         torch.cuda.synchronize()
         launches, sweeps, sweep_ms = h.stats(reset=True)
-        flops, bytes_, _ = sweep_work(h, n, nrhs, out["info"]["bytes_per_entry"])
+        plan = h.sweep_plan(nrhs)
+        if plan["tma"] == 3:
+            flops, bytes_, _ = strong_sweep_work(n, args.strong_rank, nrhs, out["info"]["bytes_per_entry"])
+        else:
+            flops, bytes_, _ = sweep_work(h, n, nrhs, out["info"]["bytes_per_entry"])
         avg = sweep_ms / max(1, sweeps)
-        out.update({"nrhs": nrhs, "apply_ms": avg, "plan": h.sweep_plan(nrhs),
+        out.update({"nrhs": nrhs, "apply_ms": avg, "plan": plan, "algorithmic_flops": flops,
+                    "algorithmic_bytes": bytes_,
                     "tflops": flops / (avg / 1e3) / 1e12, "hbm_gbs": bytes_ / (avg / 1e3) / 1e9})
     h.free()
     print(json.dumps(out))

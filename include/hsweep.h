@@ -75,9 +75,13 @@ typedef struct {
   int refine_max;    /* outer FP64 refinement steps in HSWEEP_MIXED (default 8) */
   int team;          /* CTAs per sweep team (power of two, 0 = automatic) */
   int groups;        /* right-hand sides per sweep team (1, 2, 4, 5 or 8; 0 = automatic) */
-  int sweep_kernel;  /* 0: automatic (default): the bulk-copy-staged sweep on cooperative
-                           teams where its shared-memory plan fits, else the basic sweep;
-                        1: the basic sweep that reads the factors from global memory */
+  int sweep_kernel;  /* 0: automatic (default): with strong_rank > 0 the sweep on the strongly
+                           admissible format (hsweep_strong_export) where its plan fits, then
+                           the bulk-copy-staged sweep on cooperative teams where its
+                           shared-memory plan fits, else the basic sweep;
+                        1: the basic sweep that reads the factors from global memory;
+                        2: the team sweep on the sibling-pair factors (for strong_rank > 0:
+                           the stored, recompressed expansion), else the basic sweep */
   int sweep_tc;      /* HSWEEP_MIXED team sweep, ancestor-level contractions: 0 on CUDA cores
                         (default, the faster on GB300); 1 the reductions, 2 the reductions
                         and the expansion, with mma.sync tensor-core instructions (TF32
@@ -108,9 +112,12 @@ typedef struct {
                         (eps_H still truncates below R), neighbouring leaves are dense.  Each
                         T~_m is the rank-R projection, by the randomized SVD with R + 8
                         Gaussian test vectors, of the weakly admissible inverse of S~_m
-                        (rank cap r_max); it is stored exactly in the sibling-pair factor
+                        (rank cap r_max); it is written exactly in the sibling-pair factor
                         layout with rank 3 R (L - depth) + leaf at each depth, and r_max is
-                        raised to 3 R (L - 1) + leaf when smaller (HSWEEP_ERR_ARG above 56) */
+                        raised to 3 R (L - 1) + leaf when smaller (HSWEEP_ERR_ARG above 56).
+                        The setup keeps that layout recompressed to eps_H for its own
+                        arithmetic (hsweep_export_layer), and the strongly admissible T~_m
+                        exactly in their own format for the sweep (hsweep_strong_export) */
   unsigned rsvd_seed; /* key of the Philox4x32-10 generator of those test vectors (default 0) */
   int team_threads;  /* threads per CTA of the team sweep: 512 (one CTA per SM), 256 (two CTAs
                         per SM, half the rows per CTA) or 0 (default: the launch plan chooses) */
@@ -166,6 +173,28 @@ HSWEEP_API int hsweep_rsvd_normals(uint32_t blk, uint32_t m, uint32_t seed, int 
  * Returns HSWEEP_ERR_ARG on bad sizes or NULL count pointers.
  */
 HSWEEP_API int hsweep_strong_plan(int n, int leaf, int R, int* nfar, int* nnear, int* far, int* near, int* ranks);
+
+/*
+ * The strongly admissible T~_m of a handle set up with strong_rank = R > 0 (Section 2.3,
+ * the strongly admissible case), in the format its sweep reads.  Leaf j (heap node
+ * 2^L + j, s rows; sl, sr rows in the leaves j - 1, j + 1, 0 at the ends of the layer) has
+ * its record at entries recoff[j] .. recoff[j + 1] - 1, row i at recoff[j] + i * rstride[j]:
+ *     [ T(j, j)[i, :] | T(j, j - 1)[i, :] | T(j, j + 1)[i, :] |
+ *       for d = 2..L, t = 0, 1, 2: W_{v_d, t}[i_v, 0..R) ]
+ * where v_d is the leaf's ancestor at depth d and i_v the row's index in v_d.  The
+ * interaction list of the cluster with index c at depth d (0-based from the left) is
+ * (c - 2, c + 2, c + 3) for even c and (c - 3, c - 2, c + 2) for odd c, slot t in that
+ * order (partners outside the layer: zero entries); for a well-separated pair,
+ * T(u, w) = W_{u, t(w)} W_{w, t(u)}^t.  Every block not listed is zero.
+ *   m          layer, 0 <= m < n
+ *   records    host, *nentries complex128 values, or NULL
+ *   recoff     host, 2^L + 1 entries, or NULL;  rstride: host, 2^L ints, or NULL
+ *   nentries   receives the number of entries of one layer, or NULL
+ * HSWEEP_ERR_ARG if the handle holds no such records (strong_rank = 0, or a layer was
+ * imported since the setup: the apply then uses the team sweep on the sibling-pair factors).
+ */
+HSWEEP_API int hsweep_strong_export(hsweep_t h, int m, hsw_c128* records, long long* recoff, int* rstride,
+                                    long long* nentries);
 
 /*
  * Assemble A for velocity c at angular frequency omega (Eq. sigma, Eq. helmd; PML of
@@ -300,9 +329,10 @@ HSWEEP_API int hsweep_stats(hsweep_t h, int reset, long long* launches, long lon
 /*
  * The launch plan the apply would use for nrhs right-hand sides (diagnostics):
  * out[0] the sweep kernel (0: basic, 2: bulk-copy-staged on cooperative teams exchanging
- * tagged partial sums; 1 is not used), out[1] CTAs per team, out[2] right-hand sides per team,
+ * tagged partial sums, 3: the same on the strongly admissible format; 1 is not used),
+ * out[1] CTAs per team, out[2] right-hand sides per team,
  * out[3] teams, out[4] for the basic kernel 1 when its team is the whole grid (a grid barrier),
- * for the team kernel the threads per CTA (512: one CTA per SM, 256: two), out[5] dynamic shared
+ * for the team kernels the threads per CTA (512: one CTA per SM, 256: two), out[5] dynamic shared
  * memory per CTA in bytes, out[6] largest per-step factor record of one CTA in bytes,
  * out[7] column slices per row in the expansion (0 for the basic kernel).
  */

@@ -27,7 +27,7 @@ EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_appl
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
             "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan", "hsweep_philox4x32_10",
-            "hsweep_rsvd_normals", "hsweep_strong_plan", "hsweep_setup_tuning"]
+            "hsweep_rsvd_normals", "hsweep_strong_plan", "hsweep_setup_tuning", "hsweep_strong_export"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -77,6 +77,7 @@ def load_library(path=LIB_PATH):
                                      ctypes.POINTER(ctypes.c_uint32)]),
         "hsweep_rsvd_normals": (I, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, I, I, P]),
         "hsweep_strong_plan": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), P, P, P]),
+        "hsweep_strong_export": (I, [P, I, P, ctypes.POINTER(LL), ctypes.POINTER(I), ctypes.POINTER(LL)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -290,6 +291,20 @@ class Handle:
         _check(_lib.hsweep_export_layer(self.raw, m, leaves.ctypes.data_as(ctypes.c_void_p),
                                         fac.ctypes.data_as(ctypes.c_void_p), ranks), "hsweep_export_layer")
         return leaves, fac, np.array(list(ranks), dtype=np.int32)
+
+    def strong_export(self, m):
+        """Layer m in the strongly admissible format of the strong sweep: (records, recoff,
+        rstride) as numpy arrays (hsweep_strong_export)."""
+        import numpy as np
+        nleaves = 1 << self.info()["L"]
+        ne = ctypes.c_longlong(0)
+        _check(_lib.hsweep_strong_export(self.raw, m, None, None, None, ctypes.byref(ne)), "hsweep_strong_export")
+        rec = np.zeros(ne.value, np.complex128)
+        recoff = (ctypes.c_longlong * (nleaves + 1))()
+        rstride = (ctypes.c_int * nleaves)()
+        _check(_lib.hsweep_strong_export(self.raw, m, rec.ctypes.data_as(ctypes.c_void_p), recoff, rstride,
+                                         ctypes.byref(ne)), "hsweep_strong_export")
+        return rec, np.array(list(recoff), dtype=np.int64), np.array(list(rstride), dtype=np.int64)
 
     def import_layer(self, m, leaves, fac, ranks):
         import numpy as np

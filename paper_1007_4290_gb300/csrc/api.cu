@@ -80,6 +80,7 @@ static void destroy(hsweep_s* h) {
   if (!h) return;
   hsw_setup_free(h);
   hsw_strong_free(h);
+  hsw_spack_free(h);
   hsw_krylov_free(h);
   for (auto& pr : h->ev_sweep) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
@@ -107,7 +108,7 @@ static int create_impl(const double* c_dev, double omega, int n, int pml_width, 
       !(eps_H >= 0) || opt.leaf < 2 || opt.leaf > 8 || opt.r_max < 1 || opt.r_max > 56 ||
       (opt.precision != HSWEEP_FP64 && opt.precision != HSWEEP_MIXED) || !(opt.pml_C >= 0) ||
       (opt.pml_form != 0 && opt.pml_form != 1) || opt.gmres_max_it < 1 || opt.gmres_max_it > 500 ||
-      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 1 ||
+      opt.refine_max < 1 || opt.team < 0 || opt.groups < 0 || opt.sweep_kernel < 0 || opt.sweep_kernel > 2 ||
       opt.sweep_tc < 0 || opt.sweep_tc > 2 ||
       (opt.sweep_dir != 1 && opt.sweep_dir != -1) || opt.pml_sides < 0 || opt.pml_sides > 15 ||
       opt.strong_rank < 0 || opt.strong_rank > 8 || opt.krylov_lowp < 0 || opt.krylov_lowp > 1 ||
@@ -426,6 +427,7 @@ extern "C" int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, co
   HSW_CUDA(cudaMemcpy((char*)h->d_fac + (size_t)m * h->layer_stride * h->fac_elem(), buf.data(), buf.size(),
                       cudaMemcpyHostToDevice));
   HSW_CUDA(cudaMemcpy(h->d_rank + (size_t)m * h->nnodes, rk.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice));
+  h->spack_valid = false;   // the strong sweep's records no longer describe the factors
   return hsw_pack(h, m, m + 1);
 }
 
@@ -468,7 +470,8 @@ extern "C" int hsweep_setup_tuning(hsweep_t h, double* out6) {
 
 extern "C" int hsweep_sweep_plan(hsweep_t h, int nrhs, long long* out8) {
   if (!h || !out8 || nrhs < 1) return HSWEEP_ERR_ARG;
-  if (h->opt.sweep_kernel == 0 && hsw_team_plan(h, nrhs, out8)) return HSWEEP_OK;
+  if (h->opt.sweep_kernel == 0 && h->strong_R > 0 && hsw_strong_plan_sweep(h, nrhs, out8)) return HSWEEP_OK;
+  if (h->opt.sweep_kernel != 1 && hsw_team_plan(h, nrhs, out8)) return HSWEEP_OK;
   for (int i = 0; i < 8; ++i) out8[i] = 0;
   return HSWEEP_OK;
 }

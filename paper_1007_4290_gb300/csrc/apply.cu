@@ -442,7 +442,12 @@ static int apply_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, const Sweep
 
 int hsw_apply(hsweep_s* h, const c128* r, c128* z, int nrhs) {
   if (nrhs <= 0) return HSWEEP_OK;
-  if (h->opt.sweep_kernel == 0) {
+  if (h->opt.sweep_kernel == 0 && h->strong_R > 0) {
+    bool used = false;
+    int rc = hsw_apply_strong(h, r, z, nrhs, &used);
+    if (rc != HSWEEP_OK || used) return rc;
+  }
+  if (h->opt.sweep_kernel != 1) {
     bool used = false;
     int rc = hsw_apply_team(h, r, z, nrhs, &used);
     if (rc != HSWEEP_OK || used) return rc;
@@ -460,7 +465,11 @@ static long long align_up(long long x, long long a) { return (x + a - 1) / a * a
 
 size_t hsw_apply_scratch_bytes(hsweep_s* h, int nrhs) {
   if (nrhs <= 0) return 0;
-  if (h->opt.sweep_kernel == 0) {
+  if (h->opt.sweep_kernel == 0 && h->strong_R > 0) {
+    const size_t fs = hsw_apply_strong_scratch_bytes(h, nrhs);
+    if (fs > 0) return fs;
+  }
+  if (h->opt.sweep_kernel != 1) {
     const size_t fl = hsw_apply_team_scratch_bytes(h, nrhs);
     if (fl > 0) return fl;
   }
@@ -513,7 +522,12 @@ static int apply_scratch_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, con
 int hsw_apply_scratch(hsweep_s* h, const c128* r, c128* z, int nrhs, void* scratch, size_t bytes) {
   if (nrhs <= 0) return HSWEEP_OK;
   if (hsw_apply_scratch_bytes(h, nrhs) > bytes) return HSWEEP_ERR_ARG;
-  if (h->opt.sweep_kernel == 0) {      // the same kernel hsw_apply would use
+  if (h->opt.sweep_kernel == 0 && h->strong_R > 0) {      // the same kernel hsw_apply would use
+    bool used = false;
+    int rc = hsw_apply_strong(h, r, z, nrhs, &used, scratch, bytes);
+    if (rc != HSWEEP_OK || used) return rc;
+  }
+  if (h->opt.sweep_kernel != 1) {
     bool used = false;
     int rc = hsw_apply_team(h, r, z, nrhs, &used, scratch, bytes);
     if (rc != HSWEEP_OK || used) return rc;

@@ -41,6 +41,7 @@ struct Tree {
 
 struct SetupWork;   // setup.cu
 struct StrongWork;  // strong.cu
+struct StrongPack;  // sweep_strong.cu
 struct KrylovWork;  // krylov.cu
 
 struct hsweep_s {
@@ -109,6 +110,10 @@ struct hsweep_s {
   // strong admissibility (strong.cu): rank R of the well-separated blocks, 0 = weak
   int strong_R = 0;
   StrongWork* stw = nullptr;
+  // the strongly admissible T~_m in their own format for the strong sweep (sweep_strong.cu),
+  // written by the setup; an imported layer invalidates them
+  StrongPack* spk = nullptr;
+  bool spack_valid = false;
 
   std::vector<void*> allocs;   // every device allocation owned by the handle
 
@@ -171,6 +176,14 @@ int hsw_strong_project(hsweep_s* h, int m, const void* G_F, int* G_rank, void* G
                        long long gf_entries);
 int hsw_strong_expansion_rank(int R, int L, int leaf);
 void hsw_strong_free(hsweep_s* h);
+// sweep_strong.cu: records of layer m from the expanded strongly admissible factors (setup
+// layout), the apply on them, its scratch and plan
+int hsw_spack_layer(hsweep_s* h, int m, const void* G_F, const void* G_leaf, const long long* d_gfo);
+void hsw_spack_free(hsweep_s* h);
+int hsw_apply_strong(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used, void* scratch = nullptr,
+                     size_t scratch_bytes = 0);
+size_t hsw_apply_strong_scratch_bytes(hsweep_s* h, int nrhs);
+int hsw_strong_plan_sweep(hsweep_s* h, int nrhs, long long* out8);   // 1 if the strong sweep would run
 __host__ __device__ void hsw_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 // setup.cu
 int hsw_factor(hsweep_s* h);

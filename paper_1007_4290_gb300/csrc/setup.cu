@@ -1311,6 +1311,9 @@ static int factor_impl(hsweep_s* h) {
       int rc = hsw_strong_project(h, m, G_F, w->G_rank, G_F2, w->d_gfo, w->gfo_total);
       if (rc) return rc;
       std::swap(G_F, G_F2);
+      // the records of the strong sweep, from the exact strongly admissible factors
+      rc = hsw_spack_layer(h, m, G_F, G_leaf, w->d_gfo);
+      if (rc) return rc;
       rc = recompress(w->all_nodes_off, w->all_nodes, w->all_pairs_off, w->all_pairs, 1);
       if (rc) return rc;
     }

@@ -62,3 +62,49 @@ def random_layer(n, leaf, r_max, rng, scale, full_rank_pairs=False):
         Fm[:, :r] = np.sqrt(scale / max(1, r)) * (rng.standard_normal((sz[v], r)) + 1j * rng.standard_normal((sz[v], r)))
         parts.append(Fm.T.ravel())
     return leaves, np.concatenate(parts), ranks
+
+
+def strong_to_dense(n, leaf, R, rec, recoff, rstride):
+    """Dense T from the strongly admissible records of hsweep_strong_export: per row the
+    blocks of its leaf and the neighbouring leaves, and the rows of W_{v,t}; every
+    well-separated pair (u, w) is W_{u,t(w)} W_{w,t(u)}^t."""
+    L, lo, sz = tree(n, leaf)
+    nleaves = 1 << L
+
+    def il(c):
+        return (-3, -2, 2) if c & 1 else (-2, 2, 3)
+
+    T = np.zeros((n, n), complex)
+    W = {}
+    for j in range(nleaves):
+        lam = nleaves + j
+        s = sz[lam]
+        sl = sz[lam - 1] if j > 0 else 0
+        sr = sz[lam + 1] if j < nleaves - 1 else 0
+        wb = s + sl + sr
+        for i in range(s):
+            base = int(recoff[j]) + i * int(rstride[j])
+            row = rec[base:base + wb + 3 * R * (L - 1)]
+            g = lo[lam] + i
+            T[g, lo[lam]:lo[lam] + s] += row[:s]
+            if sl:
+                T[g, lo[lam - 1]:lo[lam - 1] + sl] += row[s:s + sl]
+            if sr:
+                T[g, lo[lam + 1]:lo[lam + 1] + sr] += row[s + sl:wb]
+            for d in range(2, L + 1):
+                v = lam >> (L - d)
+                iv = lo[lam] + i - lo[v]
+                for t in range(3):
+                    o = wb + (d - 2) * 3 * R + t * R
+                    W.setdefault((v, t), np.zeros((sz[v], R), complex))[iv] = row[o:o + R]
+    for (v, t), Wv in W.items():
+        d = v.bit_length() - 1
+        vl = v - (1 << d)
+        pl = vl + il(vl)[t]
+        if not 0 <= pl < (1 << d):
+            assert not Wv.any()
+            continue
+        p = (1 << d) + pl
+        tp = il(pl).index(-il(vl)[t])
+        T[lo[v]:lo[v] + sz[v], lo[p]:lo[p] + sz[p]] += Wv @ W[(p, tp)].T
+    return T

@@ -173,3 +173,55 @@ def test_rank_two_factors_against_the_oracle_strong_factors(hs, name, prec):
         assert e_gpu <= 1.2 * e_orc + floor, (m, e_gpu, e_orc)
         assert e_both <= 2.0 * max(e_gpu, e_orc) + floor, (m, e_both, e_gpu, e_orc)
     h.free()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
+@pytest.mark.parametrize("team,groups", [(0, 0), (1, 4), (2, 4), (4, 2), (8, 1), (16, 8)])
+def test_strong_format_sweep_matches_the_exact_sweep_of_its_layers(hs, prec, tol, team, groups):
+    # the sweep on the strongly admissible format (plan kernel 3) against Algorithm 2.2 of
+    # the oracle with every T~_m rebuilt densely from the exported records; n = 127 (L = 4),
+    # teams of 1 .. 16 CTAs: no exchange, neighbours only, ancestors at 1 .. 3 depths
+    from tests.helpers import strong_to_dense
+    if prec == 0 and team == 1:
+        pytest.skip("a whole complex128 layer record (two stages) exceeds one CTA's shared memory")
+    # FP64: a random smooth medium, eps_H 1e-8 for the weak stage; mixed precision: the
+    # converging lens of the paper's PML examples (complex64 setup on the random medium
+    # grows T~_m about 25 times by layer 100 and the sweep overflows; FP64 does not)
+    if prec == 0:
+        n = 127
+        c = synth.velocity_random(n, 1 / 8, 1)
+        omega, pml, eps = 2 * np.pi * 16, 8, 1e-8
+    else:
+        w = synth.workload("pml1_n127")
+        n, c, omega, pml, eps = w["n"], w["c"], w["omega"], w["pml"], 1e-6
+    opts = hs.default_opts(precision=prec, strong_rank=2, team=team, groups=groups)
+    h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, eps, opts)
+    nr = 5
+    assert h.sweep_plan(nr)["tma"] == 3
+    rng = np.random.default_rng(7)
+    R = rng.standard_normal((nr, n * n)) + 1j * rng.standard_normal((nr, n * n))
+    Z = h.apply(torch.tensor(R, device="cuda")).cpu().numpy()
+    assert h.status()[0] == 0
+    Ts = [strong_to_dense(n, 8, 2, *h.strong_export(m)) for m in range(n)]
+    h.free()
+    disc = Discretization(c, omega, pml)
+    for s in range(nr):
+        ref = solve_exact(disc, Ts, R[s])
+        assert np.linalg.norm(Z[s] - ref) / np.linalg.norm(ref) < tol, (s, team)
+
+
+def test_strong_format_records_match_the_stored_expansion(hs):
+    # the records hold the strongly admissible T~_m; the sibling-pair store holds the same
+    # matrix recompressed to eps_H for the setup's arithmetic
+    from tests.helpers import strong_to_dense
+    n = 63
+    c = synth.velocity_random(n, 1 / 8, 2)
+    opts = hs.default_opts(precision=0, strong_rank=2)
+    h = hs.hsweep_setup(torch.tensor(c, device="cuda"), 2 * np.pi * 8, 6, 1e-10, opts)
+    inf = h.info()
+    for m in (0, n // 2, n - 1):
+        Ts = strong_to_dense(n, 8, 2, *h.strong_export(m))
+        lv, fac, rk = h.export_layer(m)
+        Tw = layer_to_dense(n, 8, inf["r_max"], lv, fac, rk)
+        assert np.linalg.norm(Ts - Tw) <= 1e-8 * np.linalg.norm(Ts), m
+    h.free()
