@@ -793,8 +793,10 @@ int resident_strong_g(const hsweep_s* h, int G, size_t smem) {
 }
 
 // team size and right-hand sides per team: the fewest rounds of 2n - 1 steps, a step
-// costing a fixed latency growing with the team's depth plus work growing with the slab's
-// rows times G (the cost model of sweep_team.cu, with the strong format's work per row)
+// costing a fixed latency growing with the team's depth, work growing with the slab's rows
+// times G, and a further latency for every extra pass of the expansion over the slab's rows
+// (more than kST / kSKS rows per CTA); coefficients from the measured apply at n = 1023
+// (64 RHS: teams of 16 CTAs with G = 8, 15.1 ms; 8 CTAs with G = 4, 16.2 ms)
 template <typename R>
 StrongConfig choose_strong(hsweep_s* h, int nrhs) {
   StrongPack* p = h->spk;
@@ -820,7 +822,8 @@ StrongConfig choose_strong(hsweep_s* h, int nrhs) {
       const int teams = std::min(ngroups, teams_cap);
       const int rounds = (ngroups + teams - 1) / teams;
       const double es = (double)sizeof(Cx<R>) / 8.0;
-      const double step = 2.5 + 0.006 * es * a.slab_max * G + 0.4 * dC + 0.01 * C;
+      const int passes = (a.slab_max * kSKS + kST - 1) / kST;
+      const double step = 2.5 + 0.006 * es * a.slab_max * G + 0.4 * dC + 0.01 * C + 1.0 * (passes - 1);
       const double cost = rounds * step;
       if (cost < best_cost - 1e-9) {
         best_cost = cost;

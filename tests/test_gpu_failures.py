@@ -96,15 +96,17 @@ def test_singular_leaf_pivot_is_reported_as_numeric(hs, prec):
     assert rr[0] < 1e-8
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_withheld_partial_sums_time_out_and_every_cta_returns(hs, prec, monkeypatch):
+@pytest.mark.parametrize("prec,strong", [(0, 0), (1, 0), (0, 2)])
+def test_withheld_partial_sums_time_out_and_every_cta_returns(hs, prec, strong, monkeypatch):
+    # strong = 2: the sweep on the strongly admissible format (its partners' sums and the
+    # neighbours' boundary rows are what CTA 1 withholds)
     n = 127
     cv = synth.velocity_random(n, 1 / 8, 2)
     omega, pml = 2 * np.pi * 8, 10
-    opts = hs.default_opts(precision=prec, team=4, groups=1)
+    opts = hs.default_opts(precision=prec, team=4, groups=1, strong_rank=strong)
     h = hs.hsweep_setup(torch.tensor(cv, device="cuda"), omega, pml, 1e-6, opts)
     plan = h.sweep_plan(1)
-    assert plan["tma"] == 2 and plan["team_ctas"] == 4, plan
+    assert plan["tma"] == (3 if strong else 2) and plan["team_ctas"] == 4, plan
     r = torch.randn(1, n * n, dtype=torch.complex128, device="cuda")
     ref = h.apply(r)
     torch.cuda.synchronize()
