@@ -99,9 +99,9 @@ def strong_sweep_work(n, R, nrhs, elem_bytes):
 # keyed by workload and right-hand sides, with the SHA-256 of the kernel source they were
 # taken on: a changed kernel reports null instead of a stale number.
 SWEEP_TRAFFIC = {
-    # profiles/sweep_team_n1023_random_64rhs_dram.md: 3.98 GB read + 1.57 GB written
-    "n1023_random/64": {"sha256": "b04e7c62c70f32ff0871025f7e90165c0ff2cd4d87d87c17caa185b508ee5fef",
-                        "bytes": 5.553e9},
+    # profiles/sweep_team_n1023_random_64rhs_dram.md: 3.982 GB read + 1.571 GB written
+    "n1023_random/64": {"sha256": "20f8ebaf461d351aef190a7d70a28a392ce98d067cf952c69be4bc5447f78606",
+                        "bytes": 5.5527e9},
 }
 TEAM_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_team.cu")
 
@@ -371,6 +371,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the plain FP64 comparator of the default run (its setup takes minutes)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline of the default run")
+    ap.add_argument("--no-strong", action="store_true",
+                    help="skip the strongly admissible sweep (R = 2) of the default run")
     ap.add_argument("--cpu-seconds", type=float, default=600.0,
                     help="longest time the CPU baseline's setup chain may run beside the GPU legs")
     ap.add_argument("--krylov-lowp", type=int, default=0,
@@ -653,6 +655,35 @@ def main():
                 "note": "the device->host copy of source 0's solution sits inside this span"}
         h64.free()
 
+    # the sweep on the strongly admissible format (strong_rank = 2, the configuration of the
+    # paper's experiments) on the same workload: its own setup, then the 64-RHS apply timed
+    # with CUDA events around each launch
+    strong = None
+    if not args.no_strong:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hst = hs.hsweep_setup(c_d, omega, pml, eps, hs.default_opts(precision=hs.MIXED, strong_rank=2))
+        torch.cuda.synchronize()
+        s_st = time.perf_counter() - t0
+        Zs = torch.empty_like(f_d)
+        for _ in range(3):
+            hst.apply(f_d, Zs)
+        hst.stats(reset=True)
+        hst.profile(True)
+        for _ in range(10):
+            hst.apply(f_d, Zs)
+        hst.profile(False)
+        _, sw_s, swms_s = hst.stats(reset=True)
+        t_s = swms_s / max(1, sw_s) / 1e3
+        fl_s, by_s, st_s = strong_sweep_work(n, 2, nrhs, info["bytes_per_entry"])
+        strong = {"R": 2, "setup_s": s_st, "launch_ms": t_s * 1e3, "plan": hst.sweep_plan(nrhs),
+                  "algorithmic_flops_per_launch": fl_s, "algorithmic_bytes_per_launch": by_s,
+                  "tflops": fl_s / t_s / 1e12, "gbs": by_s / t_s / 1e9, "stored_entries": st_s,
+                  "what": "sweep_strong_kernel on the strongly admissible records (near field + rank-2 "
+                          "interaction-list factors), 64 RHS, mixed precision"}
+        hst.free()
+        del Zs
+
     cpu, u_ref = None, None
     if cpu_job is not None:
         proc, paths, threads = cpu_job
@@ -696,6 +727,7 @@ def main():
             "sweep_launches_per_step": sweeps / args.steps,
             "roofline": roof,
             "apply_only": apply_hbm,
+            "strong_sweep": strong,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
