@@ -724,10 +724,6 @@ __global__ void __launch_bounds__(256) core_product_tc(Geo g, const Cx<float>* _
 }
 
 // Shuffle-sum within aligned groups of GW lanes (GW = 16 or 32).
-template <typename R> __device__ __forceinline__ R group_sum_r(R v, int GW) {
-  for (int o = GW >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 template <typename R> __device__ __forceinline__ Cx<R> group_sum(Cx<R> v, int GW) {
   for (int o = GW >> 1; o > 0; o >>= 1) v += shfl_xor(v, o);
   return v;
@@ -797,6 +793,16 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Cb, cons
   const int gpw = 32 / GW;                    // groups per warp
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
+    // squared column norms, exact at the start of every sweep and carried through its
+    // rounds by the rotation's own update (a rotation by tan t of the pair (p, q) with
+    // <p, q> = g maps |p|^2 to |p|^2 - t |g| and |q|^2 to |q|^2 + t |g|), so a pair's test
+    // needs only the inner product
+    for (int j = warp; j < qb; j += nw) {
+      R acc = 0;
+      for (int i = lane; i < qa; i += 32) acc += abs2(C[(long long)j * qa + i]);
+      acc = warp_sum_r(acc);
+      if (lane == 0) sig[j] = acc;
+    }
     __syncthreads();
     for (int round = 0; round < me - 1; ++round) {
       // the loop bound is uniform over the warp, so every lane reaches every shuffle
@@ -809,13 +815,11 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Cb, cons
         if (ip > iq) { int tmp = ip; ip = iq; iq = tmp; }
         Cx<R>* cp = C + (long long)(live ? ip : 0) * qa;
         Cx<R>* cq = C + (long long)(live ? iq : 0) * qa;
-        R al = 0, be = 0;
+        const R al = live ? sig[ip] : R(0), be = live ? sig[iq] : R(0);
         Cx<R> ga(0, 0);
         if (live)
-          for (int i = gl; i < qa; i += GW) {
-            al += abs2(cp[i]); be += abs2(cq[i]); cfma_conj(ga, cp[i], cq[i]);
-          }
-        al = group_sum_r(al, GW); be = group_sum_r(be, GW); ga = group_sum(ga, GW);
+          for (int i = gl; i < qa; i += GW) cfma_conj(ga, cp[i], cq[i]);
+        ga = group_sum(ga, GW);
         const R ag = sqrt(abs2(ga));
         // a column whose squared norm is below frz (relative to the largest, 1 after the
         // normalisation) stays below it under every rotation and is truncated in the end:
@@ -828,6 +832,10 @@ __global__ void svd_jacobi(Geo g, double eps, const Cx<R>* __restrict__ Cb, cons
           const R tt = fabs(z) < R(1e18) ? (z >= 0 ? R(1) : R(-1)) / (fabs(z) + sqrt(R(1) + z * z)) : R(0.5) / z;
           const R cs = R(1) / sqrt(R(1) + tt * tt), sn = tt * cs;
           const Cx<R> snc = sn * conj(e), sne = sn * e;
+          if (gl == 0) {
+            sig[ip] = fmax(R(0), al - tt * ag);
+            sig[iq] = be + tt * ag;
+          }
           for (int i = gl; i < qa; i += GW) {
             const Cx<R> x = cp[i], y = cq[i];
             cp[i] = cs * x - snc * y;

@@ -18,17 +18,18 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-# sweep_kernel 0: the cooperative-team kernel (the automatic choice at these sizes);
-# sweep_kernel 1: the basic kernel
-@pytest.mark.parametrize("n,prec,nrhs,kernel", [(64, 0, 1, 0), (127, 1, 3, 0), (127, 0, 2, 0), (127, 1, 2, 1),
-                                                (64, 0, 3, 1)])
-def test_noalloc_apply_matches_apply_twice(n, prec, nrhs, kernel):
+# sweep_kernel 0: the cooperative-team kernel (the automatic choice at these sizes; with
+# strong_rank = 2 the sweep on the strongly admissible format); sweep_kernel 1: the basic
+# kernel
+@pytest.mark.parametrize("n,prec,nrhs,kernel,strong", [(64, 0, 1, 0, 0), (127, 1, 3, 0, 0), (127, 0, 2, 0, 0),
+                                                       (127, 1, 2, 1, 0), (64, 0, 3, 1, 0), (127, 0, 2, 0, 2)])
+def test_noalloc_apply_matches_apply_twice(n, prec, nrhs, kernel, strong):
     import paper_1007_4290_gb300 as hs
     c = synth.velocity_random(n, 1 / 8, 1)
     omega, pml = 2 * np.pi * (n + 1) / 12, max(2, (n + 1) // 8)
     h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-6,
-                        hs.default_opts(precision=prec, sweep_kernel=kernel))
-    assert (h.sweep_plan(nrhs)["tma"] == 2) == (kernel == 0)
+                        hs.default_opts(precision=prec, sweep_kernel=kernel, strong_rank=strong))
+    assert h.sweep_plan(nrhs)["tma"] == (3 if strong else (2 if kernel == 0 else 0))
     for call in range(2):
         r = torch.randn(nrhs, n * n, dtype=torch.complex128, device="cuda")
         ref = h.apply(r)
