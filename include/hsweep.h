@@ -85,7 +85,8 @@ typedef struct {
   int sweep_tc;      /* HSWEEP_MIXED team sweep, ancestor-level contractions: 0 on CUDA cores
                         (default, the faster on GB300); 1 the reductions, 2 the reductions
                         and the expansion, with mma.sync tensor-core instructions (TF32
-                        operands in three parts, FP32 accumulation) */
+                        operands in three parts, FP32 accumulation); teams of at most 16 CTAs
+                        with slabs of at most 64 rows (ignored otherwise) */
   int sweep_dir;     /* +1 (default): the sweep runs over the layers from x2 = 0 upward
                         (Algorithms 2.5/2.6); -1: from x2 = 1 downward (Section 3.1, the
                         dependence on the sweeping direction).  A downward handle factors

@@ -162,7 +162,8 @@ __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const C
 
 // NT threads per CTA: 512 with one CTA per SM, or 256 with two CTAs per SM (the same
 // registers per thread; one CTA's barrier waits and latencies are covered by the other's)
-template <typename R, int G, int TC, int NT>
+// WIDE: teams of more than 16 CTAs (a sibling subtree spans more than 8 CTAs)
+template <typename R, int G, int TC, int NT, bool WIDE = false>
 __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<R> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   using M = Mac<R>;
@@ -577,18 +578,34 @@ __global__ void __launch_bounds__(NT, kThreads / NT) sweep_team_kernel(TeamArgs<
 #pragma unroll
             for (int u = 0; u < 8; ++u)
               if (u < span[j]) acc += T::value(vals[j][u]);
-            for (int u = 8; u < span[j]; ++u) {    // teams of more than 16 CTAs
-              typename T::W v = T::load(src[j] + u * cstride);
-              long long spins = 0;
-              while (!T::ok(v, tag)) {
-                if (++spins > a.wait_limit || *(volatile int*)a.status != 0) {
-                  report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
-                  *s_fail = 1;
-                  break;
+            if constexpr (WIDE) {
+              // teams of more than 16 CTAs: the remaining sources eight at a time, the eight
+              // loads in flight together
+              for (int u0 = 8; u0 < span[j]; u0 += 8) {
+                typename T::W v8[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                  if (u0 + u < span[j]) v8[u] = T::load(src[j] + (u0 + u) * cstride);
+                long long spins = 0;
+                for (;;) {
+                  bool pending = false;
+#pragma unroll
+                  for (int u = 0; u < 8; ++u)
+                    if (u0 + u < span[j] && !T::ok(v8[u], tag)) {
+                      v8[u] = T::load(src[j] + (u0 + u) * cstride);
+                      pending = true;
+                    }
+                  if (!pending) break;
+                  if (++spins > a.wait_limit || *(volatile int*)a.status != 0) {
+                    report_error(a.status, HSWEEP_ERR_TIMEOUT, m);
+                    *s_fail = 1;
+                    break;
+                  }
                 }
-                v = T::load(src[j] + u * cstride);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                  if (u0 + u < span[j]) acc += T::value(v8[u]);
               }
-              acc += T::value(v);
             }
           }
           const int d = it / rg + 1;
@@ -923,7 +940,9 @@ static TeamConfig choose_team(hsweep_s* h, int nrhs) {
 template <typename R, int G, int NT>
 static int launch_team(hsweep_s* h, const TeamConfig& cfg, TeamArgs<R>& a) {
   auto kern = sweep_team_kernel<R, G, 0, NT>;
-  if constexpr (sizeof(R) == 4 && NT == kThreads) {
+  if (cfg.C > 16) {
+    kern = sweep_team_kernel<R, G, 0, NT, true>;   // sibling subtrees of more than 8 CTAs
+  } else if constexpr (sizeof(R) == 4 && NT == kThreads) {
     if (a.tc == 1) kern = sweep_team_kernel<R, G, 1, NT>;
     if (a.tc == 2) kern = sweep_team_kernel<R, G, 2, NT>;
   }
