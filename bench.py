@@ -96,24 +96,38 @@ def strong_sweep_work(n, R, nrhs, elem_bytes):
 
 
 # DRAM bytes (read + write) of one sweep launch, from ncu captures summarised in profiles/,
-# keyed by workload and right-hand sides, with the SHA-256 of the kernel source they were
-# taken on: a changed kernel reports null instead of a stale number.
+# keyed by workload and right-hand sides, with the SHA-256 of the kernel's device code they
+# were taken on (kernel_source_digest): a changed kernel reports null instead of a stale
+# number.
 SWEEP_TRAFFIC = {
     # profiles/sweep_team_n1023_random_64rhs_dram.md: 3.980 GB read + 1.570 GB written
-    "n1023_random/64": {"sha256": "3fc85a12d5195ba5291cf993c268f8441a12ae35d45e6fb110d7080c73251ee5",
+    "n1023_random/64": {"sha256": "f009424cc0483a3a9d9d9fe38ec65557fc0283c3a29be455be5b9696fd78758d",
                         "bytes": 5.5498e9},
 }
 TEAM_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_team.cu")
+
+
+def kernel_source_digest():
+    """SHA-256 of the team sweep's device code: sweep_team.cu up to its host-side launch
+    planning (the line 'struct TeamConfig {') and the shared device helpers it includes."""
+    import hashlib
+    h = hashlib.sha256()
+    with open(TEAM_KERNEL_SRC, "rb") as fh:
+        src = fh.read()
+    cut = src.find(b"struct TeamConfig {")
+    h.update(src[:cut] if cut > 0 else src)
+    common = os.path.join(os.path.dirname(TEAM_KERNEL_SRC), "sweep_common.cuh")
+    if os.path.exists(common):
+        with open(common, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def recorded_traffic(workload, nrhs):
     rec = SWEEP_TRAFFIC.get("%s/%d" % (workload, nrhs))
     if rec is None or not os.path.exists(TEAM_KERNEL_SRC):
         return None
-    import hashlib
-    with open(TEAM_KERNEL_SRC, "rb") as fh:
-        digest = hashlib.sha256(fh.read()).hexdigest()
-    return rec["bytes"] if digest == rec["sha256"] else None
+    return rec["bytes"] if kernel_source_digest() == rec["sha256"] else None
 
 
 class ClockSampler:

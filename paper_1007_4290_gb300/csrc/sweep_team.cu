@@ -881,9 +881,12 @@ static int resident_for(const hsweep_s* h, int G, size_t smem, int nt) {
 
 // Team size C, right-hand sides per team G and threads per CTA: the fewest rounds of 2n-1
 // dependent steps, a step costing a fixed latency (exchange through L2, barriers, growing
-// with the team's depth) plus work that grows with the slab's rows times G per thread.  Two
-// CTAs of 256 threads on one SM cover each other's barrier waits and latencies: their work
-// term is weighted by kShare2 (measured, the bench's component timings).
+// slowly with the team's depth) plus work that grows with the slab's rows times G per thread.
+// Two CTAs of 256 threads on one SM cover each other's barrier waits and latencies: their
+// work term is weighted by kShare2.  Coefficients from the measured apply at n = 1023: one
+// RHS 12.6 ms with teams of 32 CTAs against 13.4 ms with 16 (complex128: 31.4 ms with 64 CTAs
+// against 35.7 ms with 32); 16 RHS 15.0 ms with 16 CTAs and G = 2 against 16.7 ms with 32 CTAs
+// and G = 4; 64 RHS 25.8 ms with 16 CTAs and G = 8.
 constexpr double kShare2 = 1.5;
 
 template <typename R>
@@ -913,7 +916,7 @@ static TeamConfig choose_team_uncached(const hsweep_s* h, int nrhs) {
         const int rounds = (ngroups + teams - 1) / teams;
         const double es = (double)sizeof(Cx<R>) / 8.0;
         const double work = 0.012 * es * a.slab_max * G * ((double)kThreads / nt) * (nt == kThreads2 ? kShare2 : 1.0);
-        const double step = 2.5 + work + 0.4 * dC + 0.01 * C;
+        const double step = 2.5 + work + 0.05 * dC + 0.01 * C;
         const double cost = rounds * step;
         if (cost < best_cost - 1e-9) {
           best_cost = cost;

@@ -91,15 +91,18 @@ def test_well_separated_blocks_of_the_factors_have_rank_at_most_R(hs, R):
     h.free()
 
 
-def test_rank_two_strong_solve_reaches_the_direct_solution(hs):
+@pytest.mark.parametrize("direction", [1, -1])
+def test_rank_two_strong_solve_reaches_the_direct_solution(hs, direction):
+    # the solve runs on the strong-format sweep (plan kernel 3) in both sweep directions
     w = synth.workload("mixed1_n127")
     n = w["n"]
     disc = Discretization(w["c"], w["omega"], w["pml"], pml_sides=w["pml_sides"])
     f = w["f"].reshape(1, n * n)
     u_ref = SparseLU(disc).solve(f[0])
     for prec in (0, 1):
-        opts = hs.default_opts(precision=prec, strong_rank=2, pml_sides=w["pml_sides"])
+        opts = hs.default_opts(precision=prec, strong_rank=2, pml_sides=w["pml_sides"], sweep_dir=direction)
         h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], 0.0, opts)
+        assert h.sweep_plan(1)["tma"] == 3
         u, it, rr = h.solve(torch.tensor(f, device="cuda"), 1e-10)
         h.free()
         u = u.cpu().numpy()[0]
