@@ -48,7 +48,8 @@ namespace {
 using namespace tma;
 using namespace sweepc;
 
-constexpr int kST = 512;                    // threads per CTA
+constexpr int kST = 512;                    // threads per CTA (one CTA per SM)
+constexpr int kST2 = 256;                   // threads per CTA of the two-CTAs-per-SM variant
 constexpr int kSKS = 8;                      // expansion: lanes per row
 constexpr long long kSWait = 1LL << 22;      // bounded waits (about a second)
 
@@ -137,8 +138,10 @@ __global__ void strong_pack(int m, int L, int leaf, int R1, const int* __restric
   }
 }
 
-template <typename R, int G>
-__global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
+// NT threads per CTA: 512 with one CTA per SM, or 256 with two (the same registers per
+// thread; one CTA's barrier waits are covered by the other's work)
+template <typename R, int G, int NT>
+__global__ void __launch_bounds__(NT, kST / NT) sweep_strong_kernel(StrongArgs<R> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   using M = Mac<R>;
   using T = Tagged<R>;
@@ -164,8 +167,8 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
   Cx<R>* oq = reinterpret_cast<Cx<R>*>(sm + a.o_oq);     // [nsub][3R][GS] the slab's own clusters
   const int nnodes = 2 << L;
 
-  for (int v = tid; v < nnodes; v += kST) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
-  for (int e = tid; e < GS; e += kST) reinterpret_cast<Cx<R>*>(sm + a.o_zero)[e] = Cx<R>(0, 0);
+  for (int v = tid; v < nnodes; v += NT) { s_lo[v] = a.lo[v]; s_sz[v] = a.sz[v]; }
+  for (int e = tid; e < GS; e += NT) reinterpret_cast<Cx<R>*>(sm + a.o_zero)[e] = Cx<R>(0, 0);
   if (tid == 0) {
     *s_fail = 0;
     s_ctr[0] = 0;
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
   const int lo_c = s_lo[vc], ns = s_sz[vc];
   const long long rec0 = a.recoff[j0];
   // static tables: per row its record offset and leaf; per leaf its table offset
-  for (int i = tid; i < ns; i += kST) {
+  for (int i = tid; i < ns; i += NT) {
     int v = vc;
     for (int d = dC; d < L; ++d) v = 2 * v + ((lo_c + i) >= s_lo[2 * v + 1] ? 1 : 0);
     const int jl = v - lam0, jj = j0 + jl;
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
   for (int xp = 0; xp < 2; ++xp) {
     int* vt = reinterpret_cast<int*>(sm + a.o_vt[xp]);
     const int x_off = (int)(a.o_x[xp] / sizeof(Cx<R>));
-    for (int e0 = tid; e0 < vtoff[nl]; e0 += kST) {
+    for (int e0 = tid; e0 < vtoff[nl]; e0 += NT) {
       int jl = 0;
       while (vtoff[jl + 1] <= e0) ++jl;
       const int e = e0 - vtoff[jl];
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
     Cx<R>* xn = xne + HL * GS;
     const int* vt = reinterpret_cast<const int*>(sm + a.o_vt[s & 1]);
     if (s == 0) {
-      for (int it = tid; it < ns * G; it += kST) {
+      for (int it = tid; it < ns * G; it += NT) {
         const int i = it / G, g = it % G;
         Cx<R> v(0, 0);
         if (g < gcount) v = cvt<R>(a.r[(long long)(g0 + g) * a.N + lo_c + i]);
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
     }
     if (pub && a.C > 1) {
       const int sf = s_sz[lam0], sla = s_sz[lam0 + nl - 1];
-      for (int it = tid; it < (sf + sla) * G; it += kST) {
+      for (int it = tid; it < (sf + sla) * G; it += NT) {
         const int row = it / G, g = it % G;
         const int side = row < sf ? 0 : 1, rr = side ? row - sf : row;
         const int i = side ? ns - sla + rr : rr;
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
       }
     }
     // ---- 2. gather --------------------------------------------------------------------
-    for (int e = tid; e < ntask * G; e += kST) {
+    for (int e = tid; e < ntask * G; e += NT) {
       const int k = e / G, g = e % G;
       const int* tk = task + 4 * k;
       const int nsrc = tk[3];
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
 
     // ---- 3. expansion -----------------------------------------------------------------
     Cx<R>* ybuf = xn;
-    for (int item = tid; item < ((ns * kSKS + 31) & ~31); item += kST) {
+    for (int item = tid; item < ((ns * kSKS + 31) & ~31); item += NT) {
       const bool live = item < ns * kSKS;
       const int ks = item % kSKS;
       const int i = live ? item / kSKS : 0;
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
     Cx<R> pw[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      const int p = tid + u * kST;
+      const int p = tid + u * NT;
       pcpl[u] = c128(0.0, 0.0);
       pin[u] = c128(0.0, 0.0);
       pw[u] = Cx<R>(0, 0);
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(kST, 1) sweep_strong_kernel(StrongArgs<R> a) {
     // ---- 4. the update of Algorithm 2.6 ------------------------------------------------
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      const int p = tid + u * kST;
+      const int p = tid + u * NT;
       if (p < ns * G) {
         const int i = p % ns, g = p / ns;
         const bool valid = g < gcount;
@@ -595,7 +598,7 @@ struct StrongPack {
   int* d_src = nullptr;
   int* d_near = nullptr;
   void* d_pack = nullptr;
-  std::vector<std::array<long long, 8>> plans;   // {nrhs, ok, dC, C, G, teams, smem, ntask}
+  std::vector<std::array<long long, 9>> plans;   // {nrhs, ok, dC, C, G, teams, smem, ntask, threads}
 };
 
 namespace {
@@ -715,18 +718,19 @@ struct StrongConfig {
   bool ok;
   int dC, C, G, nteams, ntask;
   size_t smem;
+  int nt;              // threads per CTA (kST or kST2)
 };
 
 // shared-memory plan and exchange layout for (dC, G); 0 if not supported
 template <typename R>
-size_t plan_strong(const hsweep_s* h, int dC, int G, StrongArgs<R>& a) {
+size_t plan_strong(const hsweep_s* h, int dC, int G, StrongArgs<R>& a, int nt = kST) {
   const StrongPack* p = h->spk;
   const size_t es = sizeof(Cx<R>);
   const int L = h->L, lf = h->leaf, R1 = p->R, R3 = 3 * R1;
   const int nl = 1 << (L - dC);
   const int slab_max = h->tree.maxsz(dC);
   const int GS = vstride<R>(G);
-  if (L > 14 || L < 2 || (long long)slab_max * G > (G >= 8 ? 1LL : 2LL) * kST || lf > 8) return 0;
+  if (L > 14 || L < 2 || (long long)slab_max * G > (G >= 8 ? 1LL : 2LL) * nt || lf > 8) return 0;
   auto al = [](size_t x, size_t b) { return (x + b - 1) / b * b; };
   const int nred_anc = dC >= 2 ? dC - 1 : 0;
   // the slab's own clusters are counted from depth dC + 1 (index base 2^(d - dC) - 2); a
@@ -767,72 +771,84 @@ size_t plan_strong(const hsweep_s* h, int dC, int G, StrongArgs<R>& a) {
   return o;
 }
 
-template <typename R, int G>
+template <typename R, int G, int NT>
 int resident_strong(const hsweep_s* h, size_t smem) {
-  auto kern = sweep_strong_kernel<R, G>;
+  auto kern = sweep_strong_kernel<R, G, NT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kST, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return per_sm * h->num_sms;
 }
 
-template <typename R>
+template <typename R, int NT>
 int resident_strong_g(const hsweep_s* h, int G, size_t smem) {
   switch (G) {
-    case 1: return resident_strong<R, 1>(h, smem);
-    case 2: return resident_strong<R, 2>(h, smem);
-    case 4: return resident_strong<R, 4>(h, smem);
-    default: return resident_strong<R, 8>(h, smem);
+    case 1: return resident_strong<R, 1, NT>(h, smem);
+    case 2: return resident_strong<R, 2, NT>(h, smem);
+    case 4: return resident_strong<R, 4, NT>(h, smem);
+    default: return resident_strong<R, 8, NT>(h, smem);
   }
 }
 
-// team size and right-hand sides per team: the fewest rounds of 2n - 1 steps, a step
-// costing a fixed latency growing with the team's depth, work growing with the slab's rows
-// times G, and a further latency for every extra pass of the expansion over the slab's rows
-// (more than kST / kSKS rows per CTA); coefficients from the measured apply at n = 1023
-// (64 RHS: teams of 16 CTAs with G = 8, 15.1 ms; 8 CTAs with G = 4, 16.2 ms)
+// team size, right-hand sides per team and threads per CTA: the fewest rounds of 2n - 1
+// steps, a step costing a fixed latency growing slowly with the team's size, work growing
+// with the slab's rows times G, and a further latency for every extra pass of the expansion
+// over the slab's rows (more than NT / kSKS rows per CTA of NT threads); coefficients from
+// the measured apply at n = 1023 (64 RHS: teams of 16 CTAs with G = 8, 15.1 ms; 8 CTAs with
+// G = 4, 16.2 ms; two CTAs of 256 threads per SM, 15.0-15.2 ms: no gain, so their work term
+// is weighted up; one RHS: 32 CTAs 7.4 ms, 16 CTAs 8.1 ms)
+// weight of the work term for two CTAs per SM (each CTA has half the threads)
+constexpr double kShareS2 = 1.5;
+
 template <typename R>
 StrongConfig choose_strong(hsweep_s* h, int nrhs) {
   StrongPack* p = h->spk;
   for (const auto& e : p->plans)
-    if (e[0] == nrhs) return StrongConfig{e[1] != 0, (int)e[2], (int)e[3], (int)e[4], (int)e[5], (int)e[7], (size_t)e[6]};
+    if (e[0] == nrhs)
+      return StrongConfig{e[1] != 0, (int)e[2], (int)e[3], (int)e[4], (int)e[5], (int)e[7], (size_t)e[6], (int)e[8]};
   StrongConfig best{};
   best.ok = false;
   double best_cost = 1e300;
-  const int C_pref = h->opt.team, G_pref = h->opt.groups;
+  const int C_pref = h->opt.team, G_pref = h->opt.groups, T_pref = h->opt.team_threads;
   for (int C = 1; C <= h->nleaves && C <= 2 * h->num_sms; C *= 2) {
     if (C_pref > 0 && C != C_pref) continue;
     int dC = 0;
     while ((1 << (dC + 1)) <= C) ++dC;
-    for (int G : {8, 4, 2, 1}) {
-      if (G_pref > 0 && G != G_pref) continue;
-      StrongArgs<R> a;
-      const size_t smem = plan_strong<R>(h, dC, G, a);
-      if (smem == 0 || smem > 227 * 1024) continue;
-      const int resident = resident_strong_g<R>(h, G, smem);
-      const int teams_cap = std::min(resident, 1024) / C;
-      if (teams_cap < 1) continue;
-      const int ngroups = (nrhs + G - 1) / G;
-      const int teams = std::min(ngroups, teams_cap);
-      const int rounds = (ngroups + teams - 1) / teams;
-      const double es = (double)sizeof(Cx<R>) / 8.0;
-      const int passes = (a.slab_max * kSKS + kST - 1) / kST;
-      const double step = 2.5 + 0.006 * es * a.slab_max * G + 0.4 * dC + 0.01 * C + 1.0 * (passes - 1);
-      const double cost = rounds * step;
-      if (cost < best_cost - 1e-9) {
-        best_cost = cost;
-        best = StrongConfig{true, dC, C, G, teams, a.ntask, smem};
+    for (int nt : {kST, kST2}) {
+      if (T_pref > 0 && nt != T_pref) continue;
+      for (int G : {8, 4, 2, 1}) {
+        if (G_pref > 0 && G != G_pref) continue;
+        StrongArgs<R> a;
+        const size_t smem = plan_strong<R>(h, dC, G, a, nt);
+        if (smem == 0 || smem > 227 * 1024) continue;
+        const int resident = nt == kST2 ? resident_strong_g<R, kST2>(h, G, smem) : resident_strong_g<R, kST>(h, G, smem);
+        const int teams_cap = std::min(resident, 1024) / C;
+        if (teams_cap < 1) continue;
+        if (nt == kST2 && resident < 2 * h->num_sms) continue;   // only where two CTAs fit per SM
+        const int ngroups = (nrhs + G - 1) / G;
+        const int teams = std::min(ngroups, teams_cap);
+        const int rounds = (ngroups + teams - 1) / teams;
+        const double es = (double)sizeof(Cx<R>) / 8.0;
+        const int passes = (a.slab_max * kSKS + nt - 1) / nt;
+        const double work = 0.006 * es * a.slab_max * G * ((double)kST / nt) * (nt == kST2 ? kShareS2 : 1.0);
+        const double step = 2.5 + work + 0.005 * C + 1.0 * (passes - 1);
+        const double cost = rounds * step;
+        if (cost < best_cost - 1e-9) {
+          best_cost = cost;
+          best = StrongConfig{true, dC, C, G, teams, a.ntask, smem, nt};
+        }
       }
     }
   }
   if (p->plans.size() >= 64) p->plans.erase(p->plans.begin());
-  p->plans.push_back({nrhs, best.ok ? 1 : 0, best.dC, best.C, best.G, best.nteams, (long long)best.smem, best.ntask});
+  p->plans.push_back({nrhs, best.ok ? 1 : 0, best.dC, best.C, best.G, best.nteams, (long long)best.smem, best.ntask,
+                      best.nt});
   return best;
 }
 
@@ -841,19 +857,19 @@ long long al256s(long long x) { return (x + 255) / 256 * 256; }
 template <typename R>
 void strong_scratch_need(const hsweep_s* h, int nrhs, const StrongConfig& cfg, long long* w_bytes, long long* x_bytes) {
   StrongArgs<R> a;
-  plan_strong<R>(h, cfg.dC, cfg.G, a);
+  plan_strong<R>(h, cfg.dC, cfg.G, a, cfg.nt);
   const long long es = sizeof(Cx<R>);
   *w_bytes = (long long)nrhs * h->N * es;
   *x_bytes = 2LL * cfg.nteams * cfg.C * a.xwords * cfg.G * (long long)sizeof(typename Tagged<R>::W);
 }
 
-template <typename R, int G>
+template <typename R, int G, int NT>
 int launch_strong(hsweep_s* h, const StrongConfig& cfg, StrongArgs<R>& a) {
-  auto kern = sweep_strong_kernel<R, G>;
+  auto kern = sweep_strong_kernel<R, G, NT>;
   HSW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
-  lc.blockDim = dim3(kST);
+  lc.blockDim = dim3(NT);
   lc.gridDim = dim3(cfg.C * cfg.nteams);
   lc.dynamicSmemBytes = cfg.smem;
   lc.stream = h->stream;
@@ -911,7 +927,7 @@ int apply_strong_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used,
   }
   StrongPack* p = h->spk;
   StrongArgs<R> a;
-  plan_strong<R>(h, cfg.dC, cfg.G, a);
+  plan_strong<R>(h, cfg.dC, cfg.G, a, cfg.nt);
   a.n = h->n; a.L = h->L; a.leaf = h->leaf; a.dC = cfg.dC; a.C = cfg.C; a.nteams = cfg.nteams; a.nrhs = nrhs;
   a.ngroups = (nrhs + cfg.G - 1) / cfg.G;
   a.N = h->N; a.layer_stride = p->layer_stride;
@@ -934,11 +950,20 @@ int apply_strong_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* used,
   // every exchange slot starts with the tag bit set: steps 0 and 1 expect it clear
   if (cudaMemsetAsync(xptr, 0xff, (size_t)xb, h->stream) != cudaSuccess) rc = HSWEEP_ERR_CUDA;
   if (rc == HSWEEP_OK) {
-    switch (cfg.G) {
-      case 1: rc = launch_strong<R, 1>(h, cfg, a); break;
-      case 2: rc = launch_strong<R, 2>(h, cfg, a); break;
-      case 4: rc = launch_strong<R, 4>(h, cfg, a); break;
-      default: rc = launch_strong<R, 8>(h, cfg, a); break;
+    if (cfg.nt == kST2) {
+      switch (cfg.G) {
+        case 1: rc = launch_strong<R, 1, kST2>(h, cfg, a); break;
+        case 2: rc = launch_strong<R, 2, kST2>(h, cfg, a); break;
+        case 4: rc = launch_strong<R, 4, kST2>(h, cfg, a); break;
+        default: rc = launch_strong<R, 8, kST2>(h, cfg, a); break;
+      }
+    } else {
+      switch (cfg.G) {
+        case 1: rc = launch_strong<R, 1, kST>(h, cfg, a); break;
+        case 2: rc = launch_strong<R, 2, kST>(h, cfg, a); break;
+        case 4: rc = launch_strong<R, 4, kST>(h, cfg, a); break;
+        default: rc = launch_strong<R, 8, kST>(h, cfg, a); break;
+      }
     }
   }
   h->prof = prof;
@@ -974,7 +999,7 @@ int hsw_strong_plan_sweep(hsweep_s* h, int nrhs, long long* out) {
   if (!h->spack_valid || !h->spk) return 0;
   StrongConfig cfg = h->prec == HSWEEP_FP64 ? choose_strong<double>(h, nrhs) : choose_strong<float>(h, nrhs);
   if (!cfg.ok) return 0;
-  out[0] = 3; out[1] = cfg.C; out[2] = cfg.G; out[3] = cfg.nteams; out[4] = kST;
+  out[0] = 3; out[1] = cfg.C; out[2] = cfg.G; out[3] = cfg.nteams; out[4] = cfg.nt;
   out[5] = (long long)cfg.smem; out[6] = h->spk->slab_bytes_max[cfg.dC]; out[7] = kSKS;
   return 1;
 }

@@ -179,8 +179,9 @@ def test_rank_two_factors_against_the_oracle_strong_factors(hs, name, prec):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
-@pytest.mark.parametrize("team,groups", [(0, 0), (1, 4), (2, 4), (4, 2), (8, 1), (16, 8)])
-def test_strong_format_sweep_matches_the_exact_sweep_of_its_layers(hs, prec, tol, team, groups):
+@pytest.mark.parametrize("team,groups,threads", [(0, 0, 0), (1, 4, 0), (2, 4, 0), (4, 2, 0), (8, 1, 0), (16, 8, 0),
+                                                 (8, 4, 256), (16, 8, 256)])
+def test_strong_format_sweep_matches_the_exact_sweep_of_its_layers(hs, prec, tol, team, groups, threads):
     # the sweep on the strongly admissible format (plan kernel 3) against Algorithm 2.2 of
     # the oracle with every T~_m rebuilt densely from the exported records; n = 127 (L = 4),
     # teams of 1 .. 16 CTAs: no exchange, neighbours only, ancestors at 1 .. 3 depths
@@ -197,10 +198,11 @@ def test_strong_format_sweep_matches_the_exact_sweep_of_its_layers(hs, prec, tol
     else:
         w = synth.workload("pml1_n127")
         n, c, omega, pml, eps = w["n"], w["c"], w["omega"], w["pml"], 1e-6
-    opts = hs.default_opts(precision=prec, strong_rank=2, team=team, groups=groups)
+    opts = hs.default_opts(precision=prec, strong_rank=2, team=team, groups=groups, team_threads=threads)
     h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, eps, opts)
     nr = 5
-    assert h.sweep_plan(nr)["tma"] == 3
+    plan = h.sweep_plan(nr)
+    assert plan["tma"] == 3 and (threads == 0 or plan["grid_or_threads"] == threads), plan
     rng = np.random.default_rng(7)
     R = rng.standard_normal((nr, n * n)) + 1j * rng.standard_normal((nr, n * n))
     Z = h.apply(torch.tensor(R, device="cuda")).cpu().numpy()
