@@ -120,8 +120,9 @@ typedef struct {
                         arithmetic (hsweep_export_layer), and the strongly admissible T~_m
                         exactly in their own format for the sweep (hsweep_strong_export) */
   unsigned rsvd_seed; /* key of the Philox4x32-10 generator of those test vectors (default 0) */
-  int team_threads;  /* threads per CTA of the team sweep: 512 (one CTA per SM), 256 (two CTAs
-                        per SM, half the rows per CTA) or 0 (default: the launch plan chooses) */
+  int team_threads;  /* threads per CTA of the team sweeps (on the sibling-pair factors and on
+                        the strongly admissible format): 512 (one CTA per SM), 256 (two CTAs
+                        per SM) or 0 (default: the launch plan chooses) */
   int core_kernel;   /* recompression cores C = R_a R_b^t (hsweep_setup_tuning): 0 (default) the
                         setup's autotuned choice, 1 CUDA cores, 2 tensor cores (HSWEEP_MIXED;
                         HSWEEP_FP64 always uses CUDA cores) */
