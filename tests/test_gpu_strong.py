@@ -230,3 +230,27 @@ def test_strong_format_records_match_the_stored_expansion(hs):
         Tw = layer_to_dense(n, 8, inf["r_max"], lv, fac, rk)
         assert np.linalg.norm(Ts - Tw) <= 1e-8 * np.linalg.norm(Ts), m
     h.free()
+
+
+def test_strong_format_sweep_at_n511_matches_the_exact_sweep_of_its_layers(hs):
+    # the bench's launch shape (teams of 16 CTAs, 8 RHS per team, several leaves per CTA) at
+    # n = 511 on the lens workload in mixed precision, against Algorithm 2.2 of the oracle
+    # with the dense T~_m rebuilt from the exported records
+    from tests.helpers import strong_to_dense
+    w = synth.workload("n511_lens")
+    n = w["n"]
+    opts = hs.default_opts(precision=1, strong_rank=2, team=16, groups=8)
+    h = hs.hsweep_setup(torch.tensor(w["c"], device="cuda"), w["omega"], w["pml"], w["eps_H"], opts)
+    nr = 9
+    plan = h.sweep_plan(nr)
+    assert plan["tma"] == 3 and plan["team_ctas"] == 16 and plan["rhs_per_team"] == 8, plan
+    rng = np.random.default_rng(9)
+    R = rng.standard_normal((nr, n * n)) + 1j * rng.standard_normal((nr, n * n))
+    Z = h.apply(torch.tensor(R, device="cuda")).cpu().numpy()
+    assert h.status()[0] == 0
+    Ts = [strong_to_dense(n, 8, 2, *h.strong_export(m)) for m in range(n)]
+    h.free()
+    disc = Discretization(w["c"], w["omega"], w["pml"])
+    for s in (0, nr - 1):
+        ref = solve_exact(disc, Ts, R[s])
+        assert np.linalg.norm(Z[s] - ref) / np.linalg.norm(ref) < 2e-5, s
