@@ -105,16 +105,31 @@ SWEEP_TRAFFIC = {
                         "bytes": 5.5498e9},
 }
 TEAM_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_team.cu")
+STRONG_KERNEL_SRC = os.path.join(ROOT, "paper_1007_4290_gb300", "csrc", "sweep_strong.cu")
+# the same for the sweep on the strongly admissible format (R = 2)
+STRONG_TRAFFIC = {
+    # profiles/sweep_strong_n1023_random_64rhs_dram.md: 2.633 GB read + 1.571 GB written
+    "n1023_random/64": {"sha256": "aa89544f668625962cc69cb734fa81d60f2eb37a4e08e652064cd25ebd53413a", "bytes": 4.2032e9},
+}
 
 
-def kernel_source_digest():
-    """SHA-256 of the team sweep's device code: sweep_team.cu up to its host-side launch
-    planning (the line 'struct TeamConfig {') and the shared device helpers it includes."""
+def recorded_strong_traffic(workload, nrhs):
+    rec = STRONG_TRAFFIC.get("%s/%d" % (workload, nrhs))
+    if rec is None or not os.path.exists(STRONG_KERNEL_SRC):
+        return None
+    digest = kernel_source_digest(STRONG_KERNEL_SRC, b"struct StrongPack {")
+    return rec["bytes"] if digest == rec["sha256"] else None
+
+
+def kernel_source_digest(path=None, marker=b"struct TeamConfig {"):
+    """SHA-256 of a sweep kernel's device code: its source up to the host-side part (the
+    line `marker`) and the shared device helpers it includes (sweep_common.cuh)."""
     import hashlib
+    path = path or TEAM_KERNEL_SRC
     h = hashlib.sha256()
-    with open(TEAM_KERNEL_SRC, "rb") as fh:
+    with open(path, "rb") as fh:
         src = fh.read()
-    cut = src.find(b"struct TeamConfig {")
+    cut = src.find(marker)
     h.update(src[:cut] if cut > 0 else src)
     common = os.path.join(os.path.dirname(TEAM_KERNEL_SRC), "sweep_common.cuh")
     if os.path.exists(common):
@@ -692,6 +707,7 @@ def main():
         fl_s, by_s, st_s = strong_sweep_work(n, 2, nrhs, info["bytes_per_entry"])
         strong = {"R": 2, "setup_s": s_st, "launch_ms": t_s * 1e3, "plan": hst.sweep_plan(nrhs),
                   "algorithmic_flops_per_launch": fl_s, "algorithmic_bytes_per_launch": by_s,
+                  "traffic": recorded_strong_traffic(args.workload, nrhs),
                   "tflops": fl_s / t_s / 1e12, "gbs": by_s / t_s / 1e9, "stored_entries": st_s,
                   "what": "sweep_strong_kernel on the strongly admissible records (near field + rank-2 "
                           "interaction-list factors), 64 RHS, mixed precision"}
