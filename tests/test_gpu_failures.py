@@ -33,21 +33,23 @@ def _free_bytes():
     return torch.cuda.mem_get_info()[0]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_every_allocation_failure_returns_oom_and_leaks_nothing(hs, prec, monkeypatch):
+@pytest.mark.parametrize("prec,strong", [(0, 0), (1, 0), (1, 2)])
+def test_every_allocation_failure_returns_oom_and_leaks_nothing(hs, prec, strong, monkeypatch):
+    # strong = 2: the setup also allocates the projection's plan and scratch and the
+    # strongly admissible records, and the solve runs on the strong-format sweep
     w = synth.workload("n64_const")
     n = w["n"]
     c = torch.tensor(w["c"], device="cuda")
     f = torch.tensor(w["f"][0].reshape(1, n * n), device="cuda")
     u = torch.zeros_like(f)
-    opts = hs.default_opts(precision=prec)
+    opts = hs.default_opts(precision=prec, strong_rank=strong)
     # a full run first, so that every kernel module the sequence uses is loaded
     h = hs.hsweep_setup(c, w["omega"], w["pml"], w["eps_H"], opts)
     h.solve(f, 1e-8, u=u)
     h.free()
     k, failures = 1, 0
     while True:
-        monkeypatch.setenv("HSWEEP_FAIL_ALLOC_AT", "%d:%d" % (k, prec))
+        monkeypatch.setenv("HSWEEP_FAIL_ALLOC_AT", "%d:%d:%d" % (k, prec, strong))
         free0 = _free_bytes()
         code, h = None, None
         try:
