@@ -254,3 +254,29 @@ def test_strong_format_sweep_at_n511_matches_the_exact_sweep_of_its_layers(hs):
     for s in (0, nr - 1):
         ref = solve_exact(disc, Ts, R[s])
         assert np.linalg.norm(Z[s] - ref) / np.linalg.norm(ref) < 2e-5, s
+
+
+@pytest.mark.parametrize("R", [1, 3, 5])
+def test_strong_format_sweep_for_other_ranks(hs, R):
+    # ranks other than the paper's 2: 3R = 3, 9 and 15 columns per cluster (one and two
+    # column chunks of the reductions; the expanded store of the setup caps R at 5 here),
+    # against Algorithm 2.2 of the oracle with the dense T~_m rebuilt from the exported
+    # records
+    from tests.helpers import strong_to_dense
+    n = 127
+    c = synth.velocity_random(n, 1 / 8, 3)
+    omega, pml = 2 * np.pi * 12, 8
+    opts = hs.default_opts(precision=0, strong_rank=R)
+    h = hs.hsweep_setup(torch.tensor(c, device="cuda"), omega, pml, 1e-8, opts)
+    nr = 3
+    assert h.sweep_plan(nr)["tma"] == 3
+    rng = np.random.default_rng(R)
+    Rv = rng.standard_normal((nr, n * n)) + 1j * rng.standard_normal((nr, n * n))
+    Z = h.apply(torch.tensor(Rv, device="cuda")).cpu().numpy()
+    assert h.status()[0] == 0
+    Ts = [strong_to_dense(n, 8, R, *h.strong_export(m)) for m in range(n)]
+    h.free()
+    disc = Discretization(c, omega, pml)
+    for s in range(nr):
+        ref = solve_exact(disc, Ts, Rv[s])
+        assert np.linalg.norm(Z[s] - ref) / np.linalg.norm(ref) < 1e-12, (R, s)
