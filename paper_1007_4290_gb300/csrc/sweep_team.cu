@@ -150,7 +150,10 @@ template <typename R, int G, int GS, int KSTEP = kKS>
 __device__ __forceinline__ void expand_row(typename Mac<R>::A (&acc)[G], const Cx<R>* __restrict__ F,
                                            const Cx<R>* __restrict__ V, int kbeg, int kend) {
   using M = Mac<R>;
-#pragma unroll 2
+  // not unrolled: a depth's block gives a lane only one to six columns, and the unrolled
+  // loop's remainder handling cost more than it saved (measured: 3.9 against 4.2 us of a
+  // 64-RHS step's expansion)
+#pragma unroll 1
   for (int k = kbeg; k < kend; k += KSTEP) {
     const typename M::F f = M::f(F + k);
     typename M::X v[G];
