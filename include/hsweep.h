@@ -226,6 +226,16 @@ HSWEEP_API int hsweep_create(const double* c_dev, double omega, int n, int pml_w
  * T~_m u_m, backward sweep), for nrhs vectors at once.
  *   r, z  device [nrhs][N]; r is not modified; r and z must not overlap.
  * Stream-ordered; returns after enqueue.
+ * CUDA graphs: for an upward handle (sweep_dir = +1) the call enqueues one memset of the
+ * exchange slots and one cooperative kernel launch on the handle's stream, and may be
+ * captured into a graph on that stream (replays repeat the call on the captured r and
+ * z).  A capture allocates nothing: size the handle's buffers first with one call
+ * outside the capture with at least as many right-hand sides; a capture that would
+ * need larger buffers, or of a downward handle, returns HSWEEP_ERR_ARG.  Once a capture
+ * was made, buffers that later calls outgrow are kept until hsweep_free so that the
+ * graph's pointers stay valid.  A graph must not be replayed after hsweep_free or after
+ * hsweep_import_layer (the captured launch carries the rank tables of the factors as
+ * they were), nor concurrently with other work on the handle.
  */
 HSWEEP_API int hsweep_apply(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs);
 
@@ -317,6 +327,16 @@ HSWEEP_API int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, co
                         const int* ranks);
 
 /*
+ * Moves the handle to another stream: later work of the handle is enqueued on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream), for instance a stream that can be
+ * captured into a CUDA graph (the legacy default stream cannot).  Work already enqueued
+ * stays where it is; ordering the two streams is the caller's (synchronise the old one,
+ * or make the new one wait for it).  HSWEEP_ERR_ARG on a NULL handle.  (A property of
+ * the library, not of the method.)
+ */
+HSWEEP_API int hsweep_set_stream(hsweep_t h, void* stream);
+
+/*
  * Instrumentation.  hsweep_profile(h, 1) brackets every sweep-kernel launch of the
  * apply with a pair of CUDA events on the handle's stream (0 turns it off).
  * hsweep_stats reports, since the last reset: the number of kernels this handle
@@ -372,6 +392,8 @@ HSWEEP_API int hsweep_setup_tuning(hsweep_t h, double* out6);
  *     whose GPU work overlaps (other streams, other handles, other threads) race on it.
  *   - r and z are as in hsweep_apply.  No cudaMalloc, cudaFree or allocating library
  *     routine is called.  Stream-ordered; returns after enqueue.
+ *   - It may be captured into a CUDA graph on the handle's stream at any time (no
+ *     buffers to size first), with the replay rules of hsweep_apply.
  */
 #define HSWEEP_NOALLOC_SCRATCH_BYTES (32u << 20)
 HSWEEP_API int hsweep_apply_noalloc(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs);

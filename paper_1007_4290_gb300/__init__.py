@@ -27,7 +27,8 @@ EXPORTED = ["hsweep_default_opts", "hsweep_setup", "hsweep_create", "hsweep_appl
             "hsweep_solve", "hsweep_grad", "hsweep_status", "hsweep_info", "hsweep_layer_ranks",
             "hsweep_export_layer", "hsweep_import_layer", "hsweep_free", "hsweep_profile",
             "hsweep_stats", "hsweep_apply_noalloc", "hsweep_sweep_plan", "hsweep_philox4x32_10",
-            "hsweep_rsvd_normals", "hsweep_strong_plan", "hsweep_setup_tuning", "hsweep_strong_export"]
+            "hsweep_rsvd_normals", "hsweep_strong_plan", "hsweep_setup_tuning", "hsweep_strong_export",
+            "hsweep_set_stream"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -69,6 +70,7 @@ def load_library(path=LIB_PATH):
         "hsweep_import_layer": (I, [P, I, P, P, ctypes.POINTER(I)]),
         "hsweep_free": (None, [P]),
         "hsweep_profile": (I, [P, I]),
+        "hsweep_set_stream": (I, [P, P]),
         "hsweep_stats": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]),
         "hsweep_apply_noalloc": (I, [P, P, P, I]),
         "hsweep_sweep_plan": (I, [P, I, ctypes.POINTER(LL)]),
@@ -188,6 +190,12 @@ class Handle:
         layer = ctypes.c_int(-1)
         code = _lib.hsweep_status(self.raw, ctypes.byref(layer))
         return code, layer.value
+
+    def set_stream(self, stream=None):
+        """Enqueue the handle's later work on `stream` (a torch.cuda.Stream; None: the
+        current torch stream).  Ordering against work already enqueued is the caller's."""
+        s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(_lib.hsweep_set_stream(self.raw, ctypes.c_void_p(s)), "hsweep_set_stream")
 
     def profile(self, enable=True):
         _check(_lib.hsweep_profile(self.raw, 1 if enable else 0), "hsweep_profile")

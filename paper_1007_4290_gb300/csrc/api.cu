@@ -53,6 +53,22 @@ void hsw_release(hsweep_s* h, void* p) {
     }
 }
 
+bool hsw_capturing(hsweep_s* h) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
+int hsw_regrow(hsweep_s* h, void** p, size_t bytes) {
+  if (hsw_capturing(h)) return HSWEEP_ERR_ARG;
+  if (!h->graph_held) hsw_release(h, *p);
+  *p = nullptr;
+  return hsw_alloc(h, p, bytes);
+}
+
 extern "C" int hsweep_default_opts(hsweep_opts* o) {
   if (!o) return HSWEEP_ERR_ARG;
   o->leaf = 8;
@@ -265,6 +281,16 @@ extern "C" int hsweep_apply(hsweep_t h, const hsw_c128* r, hsw_c128* z, int nrhs
   const char* zb = (const char*)z;
   size_t bytes = (size_t)nrhs * h->N * sizeof(hsw_c128);
   if (nrhs > 0 && rb < zb + bytes && zb < rb + bytes) return HSWEEP_ERR_ARG;
+  if (nrhs > 0 && hsw_capturing(h)) {
+    // stream capture: upward handles only; no timing events inside a graph
+    if (h->dir < 0) return HSWEEP_ERR_ARG;
+    h->graph_held = true;
+    const bool prof = h->prof;
+    h->prof = false;
+    const int rc = hsw_apply(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs);
+    h->prof = prof;
+    return rc;
+  }
   if (h->dir > 0 || nrhs == 0) return hsw_apply(h, reinterpret_cast<const c128*>(r), reinterpret_cast<c128*>(z), nrhs);
   // downward sweep: z = P M' P r with M' the upward sweep of the reflected problem
   int rc = hsw_flip_reserve(h, 2 * bytes);
@@ -429,6 +455,12 @@ extern "C" int hsweep_import_layer(hsweep_t h, int m, const hsw_c128* leaves, co
   HSW_CUDA(cudaMemcpy(h->d_rank + (size_t)m * h->nnodes, rk.data(), h->nnodes * sizeof(int), cudaMemcpyHostToDevice));
   h->spack_valid = false;   // the strong sweep's records no longer describe the factors
   return hsw_pack(h, m, m + 1);
+}
+
+extern "C" int hsweep_set_stream(hsweep_t h, void* stream) {
+  if (!h) return HSWEEP_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return HSWEEP_OK;
 }
 
 extern "C" int hsweep_profile(hsweep_t h, int enable) {

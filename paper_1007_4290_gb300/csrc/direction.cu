@@ -38,11 +38,11 @@ unsigned flip_grid(long long work) {
 
 int hsw_flip_reserve(hsweep_s* h, size_t bytes) {
   if (bytes <= h->flip_cap) return HSWEEP_OK;
-  hsw_release(h, h->d_flip);
-  h->d_flip = nullptr;
-  h->flip_cap = 0;
-  int rc = hsw_alloc(h, &h->d_flip, bytes);
-  if (rc) return rc;
+  int rc = hsw_regrow(h, &h->d_flip, bytes);
+  if (rc) {
+    if (!h->d_flip) h->flip_cap = 0;
+    return rc;
+  }
   h->flip_cap = bytes;
   return HSWEEP_OK;
 }

@@ -131,6 +131,10 @@ struct hsweep_s {
   // pair of CUDA events around every sweep-kernel launch on the handle's stream
   long long nlaunch = 0;
   bool prof = false;
+  // set once an apply was called while the handle's stream was being captured into a CUDA
+  // graph: from then on, buffers that later calls outgrow stay allocated until hsweep_free,
+  // because the graph's launches still point into them
+  bool graph_held = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sweep;
 
@@ -140,6 +144,12 @@ struct hsweep_s {
 // Device allocation owned by the handle; HSWEEP_ERR_OOM on failure.
 int hsw_alloc(hsweep_s* h, void** p, size_t bytes);
 void hsw_release(hsweep_s* h, void* p);
+// true while the handle's stream is being captured into a CUDA graph
+bool hsw_capturing(hsweep_s* h);
+// *p replaced by a new buffer of `bytes` (contents not kept) for the apply's scratch (the w
+// cache, the exchange slots, the reflected vectors): HSWEEP_ERR_ARG during a capture (size the
+// buffers with one call outside it); the old buffer is released unless graph_held is set
+int hsw_regrow(hsweep_s* h, void** p, size_t bytes);
 
 // assemble.cu: the operator with PMLs on the sides in pml_sides into diag/east/north
 // (and s1s2 unless null)

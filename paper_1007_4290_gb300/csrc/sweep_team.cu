@@ -1028,16 +1028,20 @@ static int apply_team_impl(hsweep_s* h, const c128* r, c128* z, int nrhs, bool* 
   } else {
     const long long need_w = (long long)nrhs * h->N;
     if (need_w > h->wcache_cap) {
-      hsw_release(h, h->d_wcache); h->d_wcache = nullptr; h->wcache_cap = 0;
-      int rc = hsw_alloc(h, &h->d_wcache, (size_t)need_w * es);
-      if (rc) return rc;
+      int rc = hsw_regrow(h, &h->d_wcache, (size_t)need_w * es);
+      if (rc) {
+        if (!h->d_wcache) h->wcache_cap = 0;
+        return rc;
+      }
       h->wcache_cap = need_w;
     }
     const long long need_x = xb / (long long)es;
     if (need_x > h->xch_cap) {
-      hsw_release(h, h->d_xch); h->d_xch = nullptr; h->xch_cap = 0;
-      int rc = hsw_alloc(h, &h->d_xch, (size_t)need_x * es);
-      if (rc) return rc;
+      int rc = hsw_regrow(h, &h->d_xch, (size_t)need_x * es);
+      if (rc) {
+        if (!h->d_xch) h->xch_cap = 0;
+        return rc;
+      }
       h->xch_cap = need_x;
     }
     wptr = h->d_wcache;

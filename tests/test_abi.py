@@ -55,6 +55,7 @@ def test_default_opts_and_argument_checks_without_gpu():
     rc = hs._lib.hsweep_setup(ctypes.c_void_p(16), 1.0, 64, 40, 1e-6, None, None, ctypes.byref(raw))
     assert rc == hs.ERR_ARG
     assert hs._lib.hsweep_apply(None, None, None, 1) == hs.ERR_ARG
+    assert hs._lib.hsweep_set_stream(None, None) == hs.ERR_ARG
     hs._lib.hsweep_free(None)
 
 
