@@ -25,6 +25,11 @@ import sys
 import threading
 import time
 
+if "--cpu-single" in sys.argv:
+    # one BLAS thread for the single-thread oracle timings (read when numpy loads BLAS)
+    for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_k] = "1"
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -309,6 +314,41 @@ def cpu_baseline_run(out_json, uref_npy, stop_file, hard_s):
         json.dump(res, fh)
 
 
+def run_cpu_single(names):
+    """The oracle on one host thread (BLAS threads = 1) for the small configurations: the
+    setup chain of Algorithm 2.5 over every layer, the sweeps of Algorithm 2.6, one whole
+    preconditioned GMRES solve of source 0 at the workload's tolerance, and the sparse
+    direct solve (O2).  One JSON line per workload; no GPU is used."""
+    from oracle.direct import SparseLU
+    from oracle.gmres import preconditioned_solve
+    from oracle.sweep_h import HSweep
+    info = host_info()
+    for name in names:
+        w = synth.workload(name)
+        t0 = time.perf_counter()
+        disc, T, sec, ent = oracle_chain(w, lambda: False)
+        setup_s = time.perf_counter() - t0
+        f0 = w["f"][0].ravel().astype(complex)
+        step_s = oracle_apply_steps(disc, T, f0)
+        H = HSweep.__new__(HSweep)
+        H.disc, H.T = disc, T
+        A = disc.matrix()
+        t0 = time.perf_counter()
+        u, it, _ = preconditioned_solve(A, H.apply, f0, w["tol"])
+        solve_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        lu = SparseLU(disc)
+        t1 = time.perf_counter()
+        u_ref = lu.solve(f0)
+        t2 = time.perf_counter()
+        err = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+        print(json.dumps({"cpu_single": name, "n": disc.n, "threads": 1, "eps_H": w["eps_H"], "tol": w["tol"],
+                          "o4_setup_s": setup_s, "o4_apply_ms": 1e3 * step_s * (2 * disc.n - 1),
+                          "o4_solve_s": solve_s, "gmres_iters": it, "rel_err_vs_direct": err,
+                          "o2_factor_s": t1 - t0, "o2_solve_s": t2 - t1,
+                          "nproc": info["nproc"], "cpu_model": info["cpu_model"]}), flush=True)
+
+
 def start_cpu_baseline(tmpdir, hard_s=600.0):
     """Launch cpu_baseline_run in a new process with BLAS threads = all host cores but two
     (left to the GPU legs' host threads and the clock sampler)."""
@@ -407,6 +447,9 @@ def main():
     ap.add_argument("--krylov-lowp", type=int, default=0,
                     help="inner GMRES of the mixed solve in FP32 arithmetic (off by default)")
     ap.add_argument("--cpu-baseline-run", nargs=4, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-single", default="",
+                    help="comma-separated workloads (n64_const,n511_lens): the oracle on one host thread "
+                         "(setup, apply, one solve, the direct solve), one JSON line each; no GPU")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload (n1023_random, n511_lens, n64_const, n2047_random)")
     ap.add_argument("--apply-only", type=int, default=0, metavar="NRHS",
@@ -443,6 +486,9 @@ def main():
     if args.cpu_baseline_run is not None:
         a = args.cpu_baseline_run
         cpu_baseline_run(a[0], a[1], a[2], float(a[3]))
+        return
+    if args.cpu_single:
+        run_cpu_single([x for x in args.cpu_single.split(",") if x])
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -1,0 +1,23 @@
+"""bench.py's single-thread oracle timings (the CPU reference figures of the small
+configurations): one JSON line per workload with the oracle's setup, apply, solve and
+direct-solve times, run on the host alone."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_cpu_single_line_for_the_smallest_workload():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-single", "n64_const"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["cpu_single"] == "n64_const" and d["n"] == 64 and d["threads"] == 1
+    assert d["o4_setup_s"] > 0 and d["o4_solve_s"] > 0 and d["o2_factor_s"] > 0
+    # eps_H = 1e-9 and tol = 1e-8: the oracle's preconditioned solve reaches the direct solution
+    assert d["gmres_iters"] <= 3
+    assert d["rel_err_vs_direct"] < 1e-7
