@@ -1,6 +1,7 @@
 // GMRES on the left-preconditioned system M A u = M f (Section 2.4), batched over
 // right-hand sides, with Arnoldi by classical Gram-Schmidt (a second pass where the
-// cancellation in the first would leave the basis too far from orthogonal), Givens
+// first lost more than half of a vector's squared norm, except at the first step of an
+// inner solve, where the loss of orthogonality is local and a tighter test applies), Givens
 // rotations on the host, and an outer loop on the FP64 residual:
 //     r = f - A u,  z = M r,  stop when ||z|| <= tol ||M f||,
 //     otherwise GMRES on M A d = z (x0 = 0) and u += d.
@@ -372,13 +373,15 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
     // classical Gram-Schmidt with selective re-orthogonalisation (Daniel, Gragg, Kaufman and
     // Stewart): the first pass reads w once for its projections and its norm; the norm after
     // the projection follows from Pythagoras, and a second pass runs (for the whole batch)
-    // only when some right-hand side needs it.  After one pass the new vector keeps a
-    // component along the basis of about u sqrt(n0 / n1) (u the rounding of the dots, n0 and
-    // n1 the squared norms before and after the projection); GMRES tolerates it while it is
-    // far below the inner target eta.  FP64 arithmetic: a second pass where
-    // 1e-15 sqrt(n0 / n1) > 1e-3 eta, i.e. n1 < (1e-12 / eta)^2 n0 (at most half the norm);
-    // M A is close to the identity here, so n0 / n1 is large but rarely that large.  FP32
-    // arithmetic (krylov_lowp): where more than half of the squared norm was lost.
+    // only when some right-hand side needs it: where more than half of the squared norm was
+    // lost, except at the first step of an inner solve in FP64 arithmetic.  With several
+    // basis vectors, classical Gram-Schmidt's loss of orthogonality compounds from step to
+    // step (M A is close to the identity, so every step cancels most of w), and the usual
+    // test is kept.  At the first step the basis is one vector and the loss is local: the new
+    // vector keeps a component along it of about u sqrt(n0 / n1) (u the rounding of the dots,
+    // n0 and n1 the squared norms before and after the projection), so a second pass runs
+    // only where 1e-15 sqrt(n0 / n1) could exceed 1e-3 eta (n1 < (1e-12 / eta)^2 n0) or the
+    // norm from Pythagoras, n0 - |h|^2, could lose more than 1e-8 of n1 (n1 < 1e-8 n0).
     std::vector<cd> hcol((size_t)nrhs * (j + 1), cd(0));
     std::vector<double> wn(nrhs, 0.0);
     bool second = false, fused = false;
@@ -395,7 +398,7 @@ static int gmres_inner(hsweep_s* h, const c128* z, int nrhs, const std::vector<d
         }
         if (run[s]) {
           const double q = eta[s] > 0 ? 1e-12 / eta[s] : 1.0;
-          const double thr = lowp ? 0.5 : std::min(0.5, q * q);
+          const double thr = (lowp || j > 0) ? 0.5 : std::min(0.5, std::max(q * q, 1e-8));
           if (!(n1 >= thr * n0)) second = true;
         }
         wn[s] = std::sqrt(std::max(0.0, n1));
