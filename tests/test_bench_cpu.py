@@ -21,3 +21,24 @@ def test_cpu_single_line_for_the_smallest_workload():
     # eps_H = 1e-9 and tol = 1e-8: the oracle's preconditioned solve reaches the direct solution
     assert d["gmres_iters"] <= 3
     assert d["rel_err_vs_direct"] < 1e-7
+
+
+def test_traffic_keys_follow_the_device_code_only(tmp_path):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    # the committed DRAM captures belong to the committed kernels: the bench line carries them
+    assert bench.recorded_traffic("n1023_random", 64) is not None
+    assert bench.recorded_strong_traffic("n1023_random", 64) is not None
+    # an edit of the host part (after the marker) keeps the key, an edit of the device part drops it
+    src = open(bench.TEAM_KERNEL_SRC, "rb").read()
+    cut = src.find(b"struct TeamConfig {")
+    assert cut > 0
+    p_host = tmp_path / "host_edit.cu"
+    p_host.write_bytes(src + b"\n// host-side edit\n")
+    p_dev = tmp_path / "device_edit.cu"
+    p_dev.write_bytes(src[:cut] + b"// device-side edit\n" + src[cut:])
+    d0 = bench.kernel_source_digest()
+    assert bench.kernel_source_digest(str(p_host)) == d0
+    assert bench.kernel_source_digest(str(p_dev)) != d0
