@@ -91,3 +91,36 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     import paper_1007_4290_gb300 as hs
     with pytest.raises(ImportError):
         hs.load_library(str(tmp_path / "libhsweep.so"))
+
+
+def test_plain_c_program_compiles_links_and_calls_the_library(tmp_path):
+    """The header is plain C (C99) and the library links from C: a program that takes the
+    default options and makes calls the library must refuse before any device work."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    lib = _lib_path()
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include "hsweep.h"\n'
+        "int main(void) {\n"
+        "  hsweep_opts o;\n"
+        "  hsweep_t h = 0;\n"
+        "  if (hsweep_default_opts(&o) != HSWEEP_OK || o.leaf != 8) return 1;\n"
+        "  if (hsweep_setup(0, 1.0, 64, 8, 1e-6, &o, 0, &h) != HSWEEP_ERR_ARG || h) return 2;\n"
+        "  if (hsweep_apply(0, 0, 0, 1) != HSWEEP_ERR_ARG) return 3;\n"
+        "  if (hsweep_set_stream(0, 0) != HSWEEP_ERR_ARG) return 4;\n"
+        "  hsweep_free(0);\n"
+        "  return 0;\n"
+        "}\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib)
+    out = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"), str(src),
+                          "-L" + libdir, "-lhsweep", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, (run.returncode, run.stderr)
