@@ -42,3 +42,31 @@ def test_traffic_keys_follow_the_device_code_only(tmp_path):
     d0 = bench.kernel_source_digest()
     assert bench.kernel_source_digest(str(p_host)) == d0
     assert bench.kernel_source_digest(str(p_dev)) != d0
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_strong_sweep_work_counts_the_near_field_and_the_interaction_lists():
+    """The algorithmic flops of the strong-format sweep's roofline: per layer step and row,
+    the dense near field (its leaf and the two neighbouring leaves) once and the R columns of
+    every block of its clusters' interaction lists (Section 2.3; the oracle's Clusters) twice
+    per right-hand side, over 2n - 1 steps."""
+    from oracle.hmatrix_strong import Clusters
+    bench = _bench()
+    for n, R, nrhs in [(31, 2, 1), (127, 2, 3), (255, 1, 2), (100, 3, 1), (1023, 2, 64)]:
+        flops, _, _ = bench.strong_sweep_work(n, R, nrhs, 8)
+        ct = Clusters(n, 8)
+        L, nl = ct.L, 1 << ct.L
+        near = far = 0
+        for i in range(nl):
+            s = ct.size(L, i)
+            near += s * sum(ct.size(L, j) for j in (i - 1, i, i + 1) if 0 <= j < nl)
+            for lev in range(1, L + 1):
+                far += s * R * len(ct.interaction_list(lev, i >> (L - lev)))
+        assert flops == 8.0 * nrhs * (2 * n - 1) * (near + 2 * far), (n, R)
