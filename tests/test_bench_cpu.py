@@ -70,3 +70,44 @@ def test_strong_sweep_work_counts_the_near_field_and_the_interaction_lists():
             for lev in range(1, L + 1):
                 far += s * R * len(ct.interaction_list(lev, i >> (L - lev)))
         assert flops == 8.0 * nrhs * (2 * n - 1) * (near + 2 * far), (n, R)
+
+
+def test_weak_sweep_work_counts_the_entries_of_the_oracle_layers():
+    """The algorithmic flops of the sibling-pair sweep's roofline, from a handle's rank table,
+    against the H-matrices of the oracle's setup (Algorithm 2.5) on the same tree: per layer
+    step the dense leaves once and both factors of every off-diagonal block (V^t x, then U q),
+    8 real flops per complex multiply-add, forward over n layers and backward over n - 1."""
+    from oracle.assemble import Discretization
+    from oracle.sweep_h import HSweep
+    import numpy as np
+    import synth
+    bench = _bench()
+    n, nrhs = 63, 2
+    disc = Discretization(synth.velocity_random(n, 1 / 8, 1), 2 * np.pi * 4, 6)
+    H = HSweep(disc, 1e-6, rmax=12)
+    L, sz = bench._tree_sizes(n)
+    assert L == H.L
+    # heap index of every node of the bisection tree by (depth, first row)
+    node, lo = {}, {1: 0}
+    for v in range(1, 1 << (L + 1)):
+        d = v.bit_length() - 1
+        if v > 1:
+            p = v // 2
+            lo[v] = lo[p] + (sz[2 * p] if v & 1 else 0)
+        node[(d, lo[v])] = v
+
+    class FakeHandle:
+        def layer_ranks(self, m):
+            rk = [0] * (1 << (L + 1))
+            for d, (r0, _), _, U, _ in H.T[m].blocks():
+                rk[node[(d, r0)]] = U.shape[1]
+            return rk
+
+    flops, _, _ = bench.sweep_work(FakeHandle(), n, nrhs, 8)
+    macs = []
+    for T in H.T:
+        leaf = sum(t.hi - t.lo for t in T.leaves() for _ in range(t.hi - t.lo))
+        lowrank = sum(U.size + V.size for _, _, _, U, V in T.blocks())
+        macs.append(leaf + lowrank)
+    expect = 8.0 * nrhs * (sum(macs) + sum(macs[:-1]))
+    assert flops == expect
