@@ -1,5 +1,7 @@
 // The C-ABI of include/hsweep.h: argument checks, handle lifetime, factor-store
-// layout, and host<->device copies of single layers.
+// layout, host<->device copies of single layers, and the rules that let the apply be
+// captured into a CUDA graph (no allocation during a capture; buffers a captured graph
+// may point into are kept until the handle is freed).
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
